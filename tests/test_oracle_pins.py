@@ -1,0 +1,378 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by
+mathematics (closed forms, invariants, library routines, brute force).
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, a swapped index) fails at least one of them.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from dec_inputs import make_workload, kuhn_lattice, node_tags
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].split()
+            if line:
+                rows.setdefault(line[0], []).append(line[1:])
+    return rows
+
+
+def _single(P):
+    T = np.array([[0, 1, 2, 3]])
+    if O.tet_volumes(P, T)[0] < 0:
+        T = np.array([[0, 1, 3, 2]])
+    E, t2e = O.edge_list(T)
+    return T, E, t2e
+
+
+# ----------------------------------------------------------------- topology
+
+def test_edge_list_brute_force():
+    wl = make_workload("lognormal64", N=4)
+    E, t2e = O.edge_list(wl.tets)
+    edges = set()
+    for t in wl.tets.tolist():
+        for a, b in itertools.combinations(t, 2):
+            edges.add((min(a, b), max(a, b)))
+    assert [tuple(e) for e in E.tolist()] == sorted(edges)
+    for t, row in zip(wl.tets.tolist(), t2e.tolist()):
+        for s, (a, b) in enumerate(O.LOCAL_EDGES):
+            assert tuple(E[row[s]]) == (min(t[a], t[b]), max(t[a], t[b]))
+
+
+def test_kuhn9_counts_and_euler():
+    g = {k: int(v[0][0]) for k, v in _golden("kuhn9_counts.txt").items()}
+    xyz, tets = kuhn_lattice(9)
+    E, _ = O.edge_list(tets)
+    F = O.face_list(tets)
+    assert (len(xyz), len(E), len(F), len(tets)) == (
+        g["nodes"], g["edges"], g["faces"], g["tets"])
+    assert len(xyz) - len(E) + len(F) - len(tets) == 1
+
+
+@pytest.mark.parametrize("name,N", [("kuhn9", 5), ("lognormal64", 6)])
+def test_d1_d0_is_zero_and_euler(name, N):
+    wl = make_workload(name, N=N)
+    E, _ = O.edge_list(wl.tets)
+    F = O.face_list(wl.tets)
+    D0 = O.d0_matrix(E, wl.n)
+    D1 = O.d1_matrix(F, E, wl.n)
+    assert abs(D1 @ D0).sum() == 0.0
+    # every edge column of d1 is non-empty and has entries +-1 only
+    assert set(np.unique(D1.data)) <= {-1.0, 1.0}
+    assert wl.n - len(E) + len(F) - wl.m == 1
+
+
+# ------------------------------------------------------------ Hodge star *1
+
+def test_right_corner_tet_closed_form():
+    g = _golden("right_corner_tet.txt")
+    P = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+    T, E, t2e = _single(P)
+    w = O.hodge_star1(P, T, E, t2e)
+    want = {(int(a), int(b)): float(v) for a, b, v in g["edge"]}
+    for e, (i, j) in enumerate(E.tolist()):
+        assert w[e] == pytest.approx(want[(i, j)], abs=1e-15)
+    dv = O.dual_volumes(P, T, E, t2e)
+    for i, v in g["dualvol"]:
+        assert dv[int(i)] == pytest.approx(float(v), abs=1e-15)
+
+
+def test_regular_tet_closed_form():
+    # regular tet of edge a: by symmetry every *1 entry is equal and the four
+    # dual cells split the volume a^3/(6 sqrt 2) equally; the pyramid relation
+    # V/4 = (1/3)(a/2) * 3 * (a w) then gives w = a / (12 sqrt 2)
+    rng = np.random.default_rng(7)
+    a = 0.37
+    P = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1.0]])
+    P *= a / np.linalg.norm(P[0] - P[1])
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    P = P @ Q.T + rng.standard_normal(3)
+    T, E, t2e = _single(P)
+    w = O.hodge_star1(P, T, E, t2e)
+    np.testing.assert_allclose(w, a / (12 * np.sqrt(2)), rtol=1e-13)
+    V = a ** 3 / (6 * np.sqrt(2))
+    np.testing.assert_allclose(O.dual_volumes(P, T, E, t2e), V / 4,
+                               rtol=1e-12)
+
+
+def test_kuhn_lattice_is_h_times_7_point_stencil():
+    # on the cubic lattice every Kuhn tet has the cell centre as
+    # circumcentre, the dual cells are the lattice cubes clipped to the
+    # domain: *1 = h * (face fraction) on axis edges, 0 on diagonals
+    N = 9
+    h = 1.0 / (N - 1)
+    xyz, tets = kuhn_lattice(N)
+    E, t2e = O.edge_list(tets)
+    w = O.hodge_star1(xyz, tets, E, t2e)
+    d = xyz[E[:, 1]] - xyz[E[:, 0]]
+    axis = (np.abs(d) > 1e-12).sum(axis=1) == 1
+    assert axis.sum() == 1944
+    np.testing.assert_allclose(w[~axis], 0.0, atol=1e-16)
+    mid = 0.5 * (xyz[E[:, 0]] + xyz[E[:, 1]])
+    frac = np.ones(len(E))
+    for ax in range(3):
+        onface = (np.abs(d[:, ax]) < 1e-12) & (
+            (mid[:, ax] == 0.0) | (mid[:, ax] == 1.0))
+        frac[onface] *= 0.5
+    np.testing.assert_allclose(w[axis], h * frac[axis], rtol=1e-13)
+
+
+def test_hodge_matches_voronoi_face_areas():
+    # library routine: Qhull's Voronoi diagram gives the dual (Voronoi) face
+    # of every interior edge of a Delaunay mesh; its area / edge length is *1
+    from scipy.spatial import Voronoi
+    wl = make_workload("lognormal64", N=7)
+    E, t2e = O.edge_list(wl.tets)
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e)
+    vor = Voronoi(wl.xyz)
+    onb = ((wl.xyz == 0.0) | (wl.xyz == 1.0)).any(axis=1)
+    index = {tuple(e): i for i, e in enumerate(E.tolist())}
+    checked = 0
+    for (p, q), rv in zip(vor.ridge_points, vor.ridge_vertices):
+        if -1 in rv or onb[p] or onb[q]:
+            continue
+        V = vor.vertices[rv]
+        c = V.mean(axis=0)
+        av = sum(np.cross(V[i] - c, V[(i + 1) % len(V)] - c)
+                 for i in range(len(V)))
+        area = 0.5 * np.linalg.norm(av)
+        e = index[(min(p, q), max(p, q))]
+        ln = np.linalg.norm(wl.xyz[p] - wl.xyz[q])
+        assert w[e] == pytest.approx(area / ln, rel=1e-10, abs=1e-15)
+        checked += 1
+    assert checked > 100
+
+
+@pytest.mark.parametrize("name,N", [("kuhn9", 6), ("lognormal64", 8)])
+def test_dual_volumes_tile_the_cube(name, N):
+    wl = make_workload(name, N=N)
+    E, t2e = O.edge_list(wl.tets)
+    dv = O.dual_volumes(wl.xyz, wl.tets, E, t2e)
+    assert dv.sum() == pytest.approx(1.0, abs=1e-13)
+    # Dirichlet energy of each coordinate field, sum_e w_e (x_j - x_i)^2:
+    # the dual cells close up inside the cube, so it reduces to the dual
+    # area of the face x = 1 (resp. y = 1, z = 1), which is 1 for k = 1
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e)
+    d = wl.xyz[E[:, 1]] - wl.xyz[E[:, 0]]
+    M = np.einsum("e,ei,ej->ij", w, d, d)
+    np.testing.assert_allclose(np.diag(M), 1.0, atol=1e-13)
+
+
+def test_conductivity_scales_each_tets_share():
+    wl = make_workload("lognormal64", N=5)
+    E, t2e = O.edge_list(wl.tets)
+    k = wl.k
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e, k)
+    # same result from per-tet single-tet stars summed with weight k_T
+    acc = np.zeros(len(E))
+    for t in range(wl.m):
+        T = wl.tets[t:t + 1]
+        e1, s1 = O.edge_list(T)
+        w1 = O.hodge_star1(wl.xyz, T, e1, s1)
+        for s in range(6):
+            acc[t2e[t, s]] += k[t] * w1[s1[0, s]]
+    np.testing.assert_allclose(w, acc, rtol=1e-12, atol=1e-16)
+
+
+# ------------------------------------------------------------------ cracks
+
+def _rho_by_line_clipping(P, disc):
+    """Independent route: intersect the disc plane with the triangle's plane
+    into a line, clip the line to the triangle (2D half-planes), then take the
+    distance from the centre to the clipped segment."""
+    c, nrm = disc[:3], disc[3:6]
+    u, v = P[1] - P[0], P[2] - P[0]
+    nt = np.cross(u, v)
+    dirv = np.cross(nrm, nt)
+    if np.linalg.norm(dirv) < 1e-14 * np.linalg.norm(nt):
+        return np.inf
+    # a point on both planes: solve [nrm; nt; dirv] x = [nrm.c; nt.P0; 0]
+    A = np.stack([nrm, nt, dirv])
+    x0 = np.linalg.solve(A, [nrm @ c, nt @ P[0], dirv @ c])
+    lo, hi = -np.inf, np.inf
+    for i in range(3):
+        a, b, o = P[i], P[(i + 1) % 3], P[(i + 2) % 3]
+        ed = b - a
+        inward = np.cross(nt, ed)
+        if inward @ (o - a) < 0:
+            inward = -inward
+        f0 = inward @ (x0 - a)
+        f1 = inward @ dirv
+        if abs(f1) < 1e-300:
+            if f0 < 0:
+                return np.inf
+            continue
+        t = -f0 / f1
+        if f1 > 0:
+            lo = max(lo, t)
+        else:
+            hi = min(hi, t)
+    if lo > hi:
+        return np.inf
+    A_, B_ = x0 + lo * dirv, x0 + hi * dirv
+    d = B_ - A_
+    tt = 0.0 if d @ d == 0 else np.clip((c - A_) @ d / (d @ d), 0, 1)
+    return np.linalg.norm(c - (A_ + tt * d))
+
+
+def test_crack_rho_against_line_clipping():
+    rng = np.random.default_rng(11)
+    P = rng.uniform(0, 1, size=(400, 3, 3))
+    rho = np.zeros(400)
+    ref = np.zeros(400)
+    discs = []
+    for q in range(400):
+        nrm = rng.standard_normal(3)
+        nrm /= np.linalg.norm(nrm)
+        disc = np.r_[rng.uniform(0, 1, 3), nrm, 0.3]
+        discs.append(disc)
+        rho[q] = O.crack_rho(P[q:q + 1], disc)[0]
+        ref[q] = _rho_by_line_clipping(P[q], disc)
+    fin = np.isfinite(ref)
+    assert fin.sum() > 100 and (~fin).sum() > 50
+    assert (np.isfinite(rho) == fin).all()
+    np.testing.assert_allclose(rho[fin], ref[fin], rtol=1e-9, atol=1e-12)
+
+
+def test_crack_rho_special_cases():
+    disc = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 1.0, 1.0])      # plane z = 0
+    tri = np.array([[[2.0, -1.0, -1.0], [2.0, 1.0, -1.0], [2.0, 0.0, 1.0]]])
+    # plane meets the triangle on x = 2, y in [-0.5, 0.5]: distance 2
+    assert O.crack_rho(tri, disc)[0] == pytest.approx(2.0)
+    flat = np.array([[[0.1, 0, 0], [0.2, 0, 0], [0.1, 0.2, 0.0]]])
+    assert O.crack_rho(flat, disc)[0] == np.inf                 # coplanar
+    above = tri + np.array([0, 0, 1.5])
+    assert O.crack_rho(above, disc)[0] == np.inf                # missed
+    touch = np.array([[[0.5, 0, 0], [0.5, 1, 1], [0.5, -1, 1.0]]])
+    assert O.crack_rho(touch, disc)[0] == pytest.approx(0.5)    # one vertex
+
+
+def test_crack_states_are_nested_and_k_eff_falls():
+    wl = make_workload("growth96", N=8, n_discs=6, n_scales=5)
+    out = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k,
+                       discs=wl.discs, scales=wl.scales, precond="fsai",
+                       rtol=1e-12)
+    first = out["first_cut"]
+    assert first.min() >= 0 and first.max() <= len(wl.scales)
+    cut_counts = [(first <= b).sum() for b in range(len(wl.scales))]
+    assert cut_counts == sorted(cut_counts) and cut_counts[-1] > 0
+    q = np.array(out["q_in"])
+    assert (np.diff(q) <= 1e-12).all() and q[-1] < q[0] < 1.0 + 1e-10
+
+
+# -------------------------------------------------------- system and solve
+
+def test_laplacian_symmetric_zero_row_sums_psd():
+    wl = make_workload("lognormal64", N=5)
+    E, t2e = O.edge_list(wl.tets)
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e, wl.k)
+    L = O.full_laplacian(wl.n, E, w)
+    assert abs(L - L.T).sum() == 0.0
+    rs = np.asarray(L.sum(axis=1)).ravel()
+    assert np.abs(rs).max() <= 1e-14 * np.abs(L.diagonal()).max()
+    ev = np.linalg.eigvalsh(L.toarray())
+    assert ev.min() > -1e-12 and abs(ev[0]) < 1e-12
+    # structural pattern = mesh graph + diagonal
+    assert L.nnz == 2 * len(E) + wl.n
+    # the entry-by-entry form equals the product d0^T diag(w) d0
+    D0 = O.d0_matrix(E, wl.n)
+    P = (D0.T @ sp.diags(w) @ D0).toarray()
+    np.testing.assert_allclose(L.toarray(), P, rtol=0, atol=1e-15)
+
+
+def test_pcg_matches_dense_solve_with_dirichlet_partition():
+    wl = make_workload("lognormal64", N=5)       # 125 nodes
+    E, t2e = O.edge_list(wl.tets)
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e, wl.k)
+    Lf = O.full_laplacian(wl.n, E, w).toarray()
+    D = wl.tags == 1
+    F = ~D
+    T0 = wl.T0[0]
+    T = T0.copy()
+    T[F] = np.linalg.solve(Lf[np.ix_(F, F)], -Lf[np.ix_(F, D)] @ T0[D])
+    for pre in ("jacobi", "fsai"):
+        out = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k,
+                           precond=pre, rtol=1e-13)
+        np.testing.assert_allclose(out["T"][0], T, rtol=0, atol=1e-11)
+        assert out["relres"][0] <= 1e-13
+
+
+def test_fsai_full_pattern_is_inverse_cholesky():
+    # with a full lower pattern the factored approximate inverse is exact:
+    # G^T G = A^-1 and G A G^T = I
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((9, 9))
+    A = X @ X.T + 9 * np.eye(9)
+    G = O.fsai_factor(sp.csr_matrix(A)).toarray()
+    assert np.allclose(np.triu(G, 1), 0.0)
+    np.testing.assert_allclose(G @ A @ G.T, np.eye(9), atol=1e-12)
+    np.testing.assert_allclose(G.T @ G, np.linalg.inv(A), atol=1e-12)
+
+
+def test_fsai_sparse_pattern_unit_diagonal():
+    wl = make_workload("lognormal64", N=6)
+    E, t2e = O.edge_list(wl.tets)
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e, wl.k)
+    L, b, _ = O.laplacian(wl.n, E, w, wl.tags, wl.T0)
+    G = O.fsai_factor(L)
+    lowpat = sp.tril(L, format="csr")
+    assert (G.indptr == lowpat.indptr).all()
+    assert (G.indices == lowpat.indices).all()
+    np.testing.assert_allclose((G @ L @ G.T).diagonal(), 1.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("name,N", [("kuhn9", None), ("lognormal64", 9)])
+def test_linear_field_is_exact_and_k_eff_is_one(name, N):
+    # Sec. 2.5 / 3.1: for constant conductivity the computed field is the
+    # linear solution and k_eff equals the prescribed conductivity
+    wl = make_workload(name, N=N)
+    out = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=None,
+                       precond=wl.precond, rtol=1e-13)
+    T = out["T"][0]
+    exact = 1.0 - wl.xyz[:, 0]
+    np.testing.assert_allclose(T, exact, atol=1e-11)
+    assert O.rms_error(wl.xyz, wl.tets, T, exact) < 1e-11
+    for key in ("q_in", "q_out", "energy"):
+        assert out[key][0] == pytest.approx(1.0, abs=1e-11)
+
+
+def test_k_eff_flux_balance_and_dirichlet_bound():
+    wl = make_workload("lognormal64", N=8)
+    out = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k,
+                       precond="fsai", rtol=1e-13)
+    qi, qo, en = out["q_in"][0], out["q_out"][0], out["energy"][0]
+    assert qi == pytest.approx(qo, rel=1e-10)
+    assert qi == pytest.approx(en, rel=1e-10)
+    # Dirichlet principle with the trial field 1 - x
+    E, w = out["E"], out["w"][0]
+    dx = wl.xyz[E[:, 1], 0] - wl.xyz[E[:, 0], 0]
+    assert qi <= np.sum(w * dx ** 2) * (1 + 1e-12)
+    # zero-flux boundary: no heat leaves through y, z faces
+    T = out["T"][0]
+    Lf = O.full_laplacian(wl.n, E, w)
+    net = Lf @ T
+    free = wl.tags != 1
+    assert np.abs(net[free]).max() < 1e-11
+
+
+def test_isolated_node_becomes_identity_row():
+    wl = make_workload("lognormal64", N=5)
+    E, t2e = O.edge_list(wl.tets)
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e)
+    free = np.flatnonzero(wl.tags == 0)[3]
+    w[(E[:, 0] == free) | (E[:, 1] == free)] = 0.0
+    L, b, iso = O.laplacian(wl.n, E, w, wl.tags, wl.T0)
+    assert iso[free] and iso.sum() == 1
+    assert L[free, free] == 1.0 and b[0, free] == 0.0
+    assert node_tags(wl.xyz)[free] == 0
