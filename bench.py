@@ -1,0 +1,393 @@
+"""Benchmark of the DEC conduction hot path on GB300.
+
+One step = the whole path on one synthetic workload, through the C ABI:
+mesh_upload (edge list, CSR structure) -> hodge_assemble (*1) ->
+laplacian_build (L, b, FSAI factor) -> solve (PCG to rel. residual 1e-10)
+-> k_eff.  Inputs are resident in HBM when a step starts; L2 is flushed
+(a 512 MiB write) between timed steps, outside the timed events.
+
+Prints ONE JSON line (rank 0).  Default workload: the 64^3 jittered
+Delaunay cube with lognormal conductivity (sigma = 1), FP64 PCG with the
+FSAI preconditioner, as specified for that configuration; the mixed
+FP32/BF16 + FP64-refinement solve on the same inputs is reported next to it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the plain FP64 reference of the
+method) on a bounded sample of the same workload, scaled to a full step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time to rel-res 1e-10 & SpMV HBM GB/s: mixed/batched vs FP64, 1 GB300"
+L2_FLUSH = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device),
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- GPU arm
+def gpu_arm(args, rank, world):
+    import torch
+    from dec_inputs import make_workload
+    from paper_2104_05999_gb300 import abi, _build
+
+    dev_id = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev_id)
+    dev = torch.device("cuda", dev_id)
+    _build.build()
+    wl = make_workload(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = abi.Context(device=dev_id, stream=stream.cuda_stream)
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d_xyz, d_tets, d_tags, d_T0 = t(wl.xyz), t(wl.tets), t(wl.tags), t(wl.T0)
+    d_k, d_discs = t(wl.k), t(wl.discs)
+    d_scales = t(wl.scales)
+    flush = torch.empty(L2_FLUSH, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    pc = abi.DEC_PRECOND_FSAI if wl.precond == "fsai" else abi.DEC_PRECOND_JACOBI
+    rtol = 1e-10
+
+    # pinned host copies for the end-to-end measurement
+    pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    h_xyz, h_tets, h_tags, h_T0 = pin(wl.xyz), pin(wl.tets), pin(wl.tags), pin(wl.T0)
+    h_k, h_discs, h_scales = pin(wl.k), pin(wl.discs), pin(wl.scales)
+
+    def step(mode, host=False, T_out=None):
+        src = wl if host else None
+        if host:
+            ctx.dec_mesh_upload(h_xyz, h_tets, h_tags)
+            ctx.dec_hodge_assemble(h_k, h_discs, h_scales)
+            ctx.dec_laplacian_build(h_T0, pc)
+        else:
+            ctx.dec_mesh_upload(d_xyz, d_tets, d_tags)
+            ctx.dec_hodge_assemble(d_k, d_discs, d_scales)
+            ctx.dec_laplacian_build(d_T0, pc)
+        st, iters, relres = ctx.dec_solve(rtol, 100000, mode, T_out)
+        q_in, q_out, en = ctx.dec_k_eff()
+        del src
+        return iters, relres, q_in
+
+    def timed(mode, steps, warmup, host=False):
+        T_out = None
+        if host:
+            T_out = torch.empty((wl.batch, wl.n), dtype=torch.float64).pin_memory()
+        for _ in range(warmup):
+            step(mode, host, T_out)
+        times = []
+        launches0 = ctx.dec_get_launch_count()
+        res = None
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            res = step(mode, host, T_out)
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        launches = (ctx.dec_get_launch_count() - launches0) / max(steps, 1)
+        return times, res, launches
+
+    want = wl.mode if args.mode == "auto" else args.mode
+    mode64 = abi.DEC_MODE_FP64 if want == "fp64" else abi.DEC_MODE_MIXED
+    other = abi.DEC_MODE_MIXED if mode64 == abi.DEC_MODE_FP64 else abi.DEC_MODE_FP64
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev_id) as clk:
+        times, (iters, relres, q_in), launches = timed(mode64, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    ms = statistics.mean(times)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # the other precision on the same inputs (comparison, fewer steps)
+    o_times, (o_iters, o_relres, o_q), _ = timed(other, max(2, args.steps // 2), 1)
+    # end to end through host buffers (H2D of the inputs, D2H of T and k_eff)
+    e_times, _, _ = timed(mode64, max(2, args.steps // 2), 1, host=True)
+    h2d = (wl.xyz.nbytes + wl.tets.nbytes + wl.tags.nbytes + wl.T0.nbytes +
+           (wl.k.nbytes if wl.k is not None else 0) +
+           (wl.discs.nbytes if wl.discs is not None else 0))
+    d2h = wl.batch * wl.n * 8 + 3 * 8 * wl.batch
+
+    # solve-only timing: time dec_solve alone (assembly already done)
+    step(mode64)
+    s_times = []
+    for _ in range(3):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        ctx.dec_solve(rtol, 100000, mode64, None)
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        e1.synchronize()
+        s_times.append(e0.elapsed_time(e1))
+
+    # roofline of the dominant kernel: cold-L2 launches of the CSR SpMV
+    n, m, ne, nnz, B = ctx.sizes()
+    spmv_ms = ctx.dec_time_kernel(abi.DEC_KERNEL_SPMV_F64, reps=20)
+    spmv32_ms = ctx.dec_time_kernel(abi.DEC_KERNEL_SPMV_F32, reps=20)
+    fsai_ms = fsai16_ms = None
+    if pc == abi.DEC_PRECOND_FSAI:
+        fsai_ms = ctx.dec_time_kernel(abi.DEC_KERNEL_FSAI_F64, reps=20)
+        fsai16_ms = ctx.dec_time_kernel(abi.DEC_KERNEL_FSAI_BF16, reps=20)
+    bytes64 = 12 * nnz + 4 * (n + 1) + 16 * n
+    bytes32 = 8 * nnz + 4 * (n + 1) + 8 * n
+    nnz_g = (nnz + n) // 2
+    fsai_bytes64 = 2 * (12 * nnz_g + 4 * (n + 1) + 16 * n) + 8 * n
+    fsai_bytes16 = 2 * (6 * nnz_g + 4 * (n + 1) + 8 * n) + 4 * n
+    peak, peak_kind = _peaks()
+    gbs = bytes64 / (spmv_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "spmv_f64_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                tj = json.load(f)
+            if tj.get("workload") == wl.name and tj.get("kernel_rev") == KERNEL_REV:
+                traffic = tj["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    clocks = clk.summary()
+
+    out = {
+        "metric": METRIC, "value": round(ms, 4), "unit": "ms",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded jittered-lattice Delaunay mesh, lognormal k)",
+        "config": {"workload": wl.name, "n_nodes": n, "n_tets": m,
+                   "n_edges": ne, "nnz": nnz, "instances": B,
+                   "precond": wl.precond,
+                   "mode": "fp64" if mode64 == abi.DEC_MODE_FP64 else "mixed",
+                   "rtol": rtol, "l2": "flushed (512 MiB write) between steps",
+                   "step": "mesh_upload+hodge+laplacian+FSAI+PCG+k_eff"},
+        "iters": int(iters[0]), "relres": float(relres[0]),
+        "k_eff": float(q_in[0]),
+        "solve_ms": round(statistics.mean(s_times), 4),
+        "other_mode": {"mode": "mixed" if other == abi.DEC_MODE_MIXED else "fp64",
+                       "ms_per_step": round(statistics.mean(o_times), 4),
+                       "iters": int(o_iters[0]), "relres": float(o_relres[0]),
+                       "k_eff_rel_diff": abs(float(o_q[0]) - float(q_in[0])) / abs(float(q_in[0]))},
+        "kernels_ms": {"spmv_f64": spmv_ms, "spmv_f32": spmv32_ms,
+                       "fsai_apply_f64": fsai_ms, "fsai_apply_bf16": fsai16_ms},
+        "kernels_gbs": {
+            "spmv_f64": round(bytes64 / (spmv_ms * 1e-3) / 1e9, 1),
+            "spmv_f32": round(bytes32 / (spmv32_ms * 1e-3) / 1e9, 1),
+            "fsai_apply_f64": round(fsai_bytes64 / (fsai_ms * 1e-3) / 1e9, 1) if fsai_ms else None,
+            "fsai_apply_bf16": round(fsai_bytes16 / (fsai16_ms * 1e-3) / 1e9, 1) if fsai16_ms else None},
+        "roofline": {"kernel": "spmv_pq_kernel<8,double,double> (CSR SpMV + p.q)",
+                     "bound": "hbm", "achieved": round(gbs, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                     "peak_kind": f"{peak_kind} burst copy",
+                     "traffic": traffic,
+                     "algorithmic_bytes": bytes64},
+        "e2e": {"value": round(statistics.mean(e_times), 4), "unit": "ms",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(round(launches)),
+        "clocks": clocks,
+    }
+    ctx.close()
+    return out
+
+
+KERNEL_REV = "r1"
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(wl, m_sample, pcg_iters, target_iters):
+    """Time the oracle's full path on the sub-mesh made of the first
+    ``m_sample`` tets (a slab of the lattice-ordered mesh) and scale every
+    piece linearly to the full mesh; PCG time per iteration is measured over
+    ``pcg_iters`` iterations and scaled to ``target_iters``.  Returns
+    (ms per full step, description)."""
+    import oracle as O
+    tets = wl.tets[:m_sample]
+    used = np.unique(tets)
+    remap = -np.ones(wl.n, dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    sub_tets = remap[tets].astype(np.int32)
+    xyz = wl.xyz[used]
+    tags = wl.tags[used]
+    T0 = wl.T0[0][used]
+    k = None if wl.k is None else wl.k[:m_sample]
+    ns = len(used)
+    t0 = time.perf_counter()
+    E, t2e = O.edge_list(sub_tets)
+    w = O.hodge_star1(xyz, sub_tets, E, t2e, k)
+    L, b, _ = O.laplacian(ns, E, w, tags, T0)
+    t1 = time.perf_counter()
+    if wl.precond == "fsai":
+        G = O.fsai_factor(L)
+        Gt = G.T.tocsr()
+        M = lambda r: Gt @ (G @ r)  # noqa: E731
+    else:
+        d = O.jacobi(L)
+        M = lambda r: d * r  # noqa: E731
+    t2 = time.perf_counter()
+    O.pcg(L, b[0], M, rtol=1e-300, max_iter=pcg_iters)
+    t3 = time.perf_counter()
+    Tfull = np.zeros(ns)
+    O.k_eff(xyz, E, w, Tfull, tags)
+    t4 = time.perf_counter()
+    fm = wl.m / m_sample
+    fn = wl.n / ns
+    ms = 1e3 * ((t1 - t0) * fm + (t2 - t1) * fn +
+                (t3 - t2) / pcg_iters * fn * target_iters + (t4 - t3) * fn)
+    desc = (f"oracle (numpy/scipy FP64, 1 thread) on the first {m_sample} of "
+            f"{wl.m} tets ({ns} nodes); assembly and preconditioner setup "
+            f"scaled linearly to the full mesh, {pcg_iters} PCG iterations "
+            f"timed and scaled to {target_iters} iterations on the full mesh")
+    return ms, desc
+
+
+def reference_arm(args):
+    from dec_inputs import make_workload
+    wl = make_workload(args.workload)
+    target = args.ref_iters
+    times = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        ms, desc = oracle_sample(wl, args.ref_tets, 10, target)
+        if i >= args.warmup:
+            times.append(ms)
+    ms = statistics.mean(times)
+    return {
+        "metric": METRIC, "value": round(ms, 2), "unit": "ms", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": wl.name, "precond": wl.precond, "mode": "fp64",
+                   "rtol": 1e-10},
+        "cpu_baseline": {"value": round(ms, 2), "unit": "ms", "cores": 1,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(ms, 2), "unit": "ms", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="lognormal64")
+    ap.add_argument("--mode", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-tets", type=int, default=60000)
+    ap.add_argument("--ref-iters", type=int, default=300)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference_arm(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    out = gpu_arm(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            from dec_inputs import make_workload
+            wl = make_workload(args.workload)
+            ms, desc = oracle_sample(wl, 4 * args.ref_tets, 20, out["iters"])
+            out["cpu_baseline"] = {"value": round(ms, 1), "unit": "ms",
+                                   "cores": 1, "kind": "oracle",
+                                   "sample": desc}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

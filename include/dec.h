@@ -1,0 +1,227 @@
+/*
+ * dec.h - C ABI of the GB300 DEC steady-conduction library (libdec_gb300).
+ *
+ * The library computes, on one GPU, the data-parallel hot path of the
+ * discrete exterior calculus (DEC) method for 3D elliptic boundary value
+ * problems of arXiv 2104.05999 ("Parallelized DEC for three-dimensional
+ * elliptic problems"), with steady heat conduction as the proxy problem:
+ *
+ *   dec_mesh_upload      cells and incidence: the edge list of the
+ *                        tetrahedral complex, i.e. the sparsity of d0
+ *                        (Sec. 2.1, cell complexes and coboundary d)
+ *   dec_hodge_assemble   diagonal Hodge star *1 on edges from the
+ *                        circumcentric dual, times conductivity, zeroed on
+ *                        dual faces that a penny crack cuts (Sec. 2.1, 2.5)
+ *   dec_laplacian_build  node Laplacian L = d0^T *1 d0 with Dirichlet rows
+ *                        and zero-flux (natural) boundaries (Sec. 2.3,
+ *                        Eq. 11-13) plus a sparse-approximate-inverse
+ *                        preconditioner (Sec. 2.3, ParaSails family)
+ *   dec_solve            preconditioned conjugate gradients to a relative
+ *                        residual (Sec. 2.3, Sec. 3.1)
+ *   dec_k_eff            effective conductivity: heat flux through the
+ *                        Dirichlet face x = 0 (Sec. 2.5)
+ *
+ * Conventions for every entry point:
+ *   - Return value: a dec_status; DEC_OK (0) on success.  No call aborts.
+ *     dec_last_error() returns a text for the last failure of a context.
+ *   - Pointers marked "host or device" may point to host memory (pageable or
+ *     pinned) or to device memory of the context's GPU; copies use unified
+ *     addressing.  Input buffers are copied: the caller keeps ownership and
+ *     may free or reuse them when the call returns.  Output buffers are
+ *     allocated by the caller and written before the call returns.
+ *   - All GPU work is ordered on the stream given to dec_create.  A call
+ *     returns once its outputs are valid; host-side scalars it returns are
+ *     synchronised.
+ *   - Calls must come in order: mesh_upload, hodge_assemble,
+ *     laplacian_build, solve, k_eff.  A call made before its predecessor
+ *     returns DEC_ERR_STATE.  A new mesh_upload invalidates everything after
+ *     it; a new hodge_assemble invalidates the Laplacian and the solution.
+ *   - Device memory is owned by the context and reused across calls while
+ *     sizes allow; dec_destroy frees it.
+ *   - Index types: node ids are int32 (n < 2^31 - 1), counts are int64.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef DEC_GB300_H
+#define DEC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dec_ctx dec_ctx;
+
+typedef enum {
+  DEC_OK = 0,
+  DEC_ERR_ARG = 1,          /* invalid argument (NULL, size, enum value)    */
+  DEC_ERR_MESH = 2,         /* node id out of range, inverted or flat tet   */
+  DEC_ERR_CUDA = 3,         /* a CUDA runtime call failed (text has it)     */
+  DEC_ERR_BREAKDOWN = 4,    /* CG breakdown: p^T L p <= 0 or not finite     */
+  DEC_NOT_CONVERGED = 5,    /* max_iter reached before rtol                 */
+  DEC_ERR_TIMEOUT = 6,      /* a bounded device-side wait ran out           */
+  DEC_ERR_STATE = 7,        /* entry point called out of order              */
+  DEC_ERR_LIMIT = 8         /* a size exceeds a documented limit            */
+} dec_status;
+
+/* node tags (node_tag argument of dec_mesh_upload) */
+enum { DEC_NODE_FREE = 0, DEC_NODE_DIRICHLET = 1, DEC_NODE_NEUMANN = 2 };
+/* preconditioners (dec_laplacian_build) */
+enum { DEC_PRECOND_JACOBI = 0, DEC_PRECOND_FSAI = 1 };
+/* solve modes (dec_solve) */
+enum {
+  DEC_MODE_FP64 = 0,   /* PCG in FP64 (matrix, preconditioner, vectors)       */
+  DEC_MODE_MIXED = 1   /* FP32 PCG with a BF16 FSAI factor (FP32 Jacobi)
+                          inside FP64 defect correction: r = b - L x in FP64,
+                          inner solve of L e = r in FP32, x += e             */
+};
+
+/* Local edge slots of a tet: slot s joins local vertices LOCAL[s] =
+ * (0,1) (0,2) (0,3) (1,2) (1,3) (2,3).  t2e[t*6+s] is that edge's id. */
+
+/* Create a context on CUDA device `device`, ordering its work on `stream`
+ * (a cudaStream_t of that device).  With stream = NULL the context creates a
+ * private non-blocking stream; device inputs must then be complete when a
+ * call is made.  *ctx receives the handle. */
+dec_status dec_create(dec_ctx** ctx, int device, void* stream);
+
+/* Free every device buffer of the context and the context itself.
+ * Accepts NULL. */
+dec_status dec_destroy(dec_ctx* ctx);
+
+/* Text of the last error of `ctx` (or of the last failed dec_create when
+ * ctx is NULL).  Valid until the next call on the context. */
+const char* dec_last_error(const dec_ctx* ctx);
+
+/* Upload a tetrahedral mesh and build its edge list (the incidence d0 of
+ * Sec. 2.1) on the GPU.
+ *   xyz      [n_nodes*3] f64, host or device: node coordinates x, y, z.
+ *   tets     [n_tets*4] int32, host or device: node ids of each tet,
+ *            positively oriented ((x1-x0).((x2-x0)x(x3-x0)) > 0).
+ *   node_tag [n_nodes] uint8, host or device: DEC_NODE_* per node.
+ * Edges come out unique with i < j, sorted by (i, j).  Errors:
+ * DEC_ERR_ARG for NULL pointers, n_nodes < 4 or >= 2^31 - 1, n_tets < 1 or
+ * 6*n_tets >= 2^32; DEC_ERR_MESH when a node id is out of range, a tet is
+ * not positively oriented, or a tag is not 0, 1 or 2. */
+dec_status dec_mesh_upload(dec_ctx* ctx, const double* xyz, int64_t n_nodes,
+                           const int32_t* tets, int64_t n_tets,
+                           const uint8_t* node_tag);
+
+/* Assemble the diagonal Hodge star *1 on edges (Sec. 2.1: ratio of the
+ * circumcentric dual face area to the edge length, signed pieces), with
+ * each tet's share scaled by its conductivity, and the crack state of
+ * every edge (Sec. 2.5: a cracked dual face gets conductivity 0).
+ *   k        [n_tets] f64 host or device, or NULL for k = 1.  Must be
+ *            finite and > 0.
+ *   discs    [n_discs*7] f64 host or device (cx, cy, cz, nx, ny, nz, r),
+ *            unit normals, r > 0; NULL with n_discs = 0 for no cracks.
+ *   scales   [n_scales] f64 host or device, increasing radius factors of
+ *            the crack states of one disc population, or NULL (one state,
+ *            factor 1).  n_scales <= 255.
+ * An edge is cut in state b when a disc with radius scales[b]*r meets a
+ * sub-triangle (midpoint, face circumcentre, tet circumcentre) of its dual
+ * face; the whole edge then gets *1 = 0 in that state.
+ * Errors: DEC_ERR_STATE without a mesh, DEC_ERR_ARG for bad k, discs or
+ * scales. */
+dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k,
+                              const double* discs, int64_t n_discs,
+                              const double* scales, int32_t n_scales);
+
+/* Build the node Laplacian and the right-hand sides (Sec. 2.3, Eq. 11-13),
+ * node form: L_ij = -*1_ij, L_ii = sum_j *1_ij; Dirichlet columns move to
+ * the right-hand side (b_i = sum_{j in D} *1_ij T0_j), Dirichlet rows
+ * become identity rows with b_i = 0 (the unknown is T - T0 on Dirichlet
+ * nodes, i.e. 0); a free row whose weights are all zero becomes an
+ * identity row too.  Then set up the preconditioner.
+ *   T0       [n_sets*n_nodes] f64 host or device: Dirichlet values (only
+ *            entries at Dirichlet nodes are read).
+ *   n_sets   number of Dirichlet value sets (right-hand sides), >= 1.
+ *            With n_scales > 1 in dec_hodge_assemble, n_sets must be 1: the
+ *            instances are then the crack states.
+ *   precond  DEC_PRECOND_JACOBI or DEC_PRECOND_FSAI (factored sparse
+ *            approximate inverse on the pattern of lower(L): G^T G ~ L^-1).
+ * Errors: DEC_ERR_STATE, DEC_ERR_ARG, DEC_ERR_LIMIT when an FSAI row has
+ * more than 32 lower-pattern entries (a node with more than 31 neighbours of
+ * smaller id). */
+dec_status dec_laplacian_build(dec_ctx* ctx, const double* T0, int32_t n_sets,
+                               int32_t precond);
+
+/* Solve L u = b for every instance by PCG from u = 0 until
+ * ||b - L u||_2 <= rtol ||b||_2 (FP64 true residual), then form the
+ * temperature T = u + T0 on Dirichlet nodes.
+ *   rtol      relative residual, > 0 (e.g. 1e-10).
+ *   max_iter  cap on (inner) CG iterations per instance, >= 1.
+ *   mode      DEC_MODE_FP64 or DEC_MODE_MIXED.
+ *   T_out     [B*n_nodes] f64 host or device, or NULL to keep T on the GPU
+ *             only (k_eff still works).  B = number of instances.
+ *   iters     [B] int32 host, or NULL: CG iterations used per instance.
+ *   relres    [B] f64 host, or NULL: final FP64 relative residuals.
+ * Errors: DEC_ERR_STATE, DEC_ERR_ARG, DEC_ERR_BREAKDOWN, DEC_NOT_CONVERGED
+ * (outputs are still written with the last iterate). */
+dec_status dec_solve(dec_ctx* ctx, double rtol, int32_t max_iter, int32_t mode,
+                     double* T_out, int32_t* iters, double* relres);
+
+/* Effective conductivity per instance (Sec. 2.5) from the last solve, in
+ * FP64 with the unmodified *1 (cut edges 0):
+ *   q_in   [B] host: sum over Dirichlet nodes on x = 0 of sum_j *1_ij (T_i - T_j)
+ *   q_out  [B] host or NULL: same over x = 1 with (T_j - T_i)
+ *   energy [B] host or NULL: sum over edges of *1_e (T_i - T_j)^2
+ * For T0 = 1 on x = 0 and 0 on x = 1 in the unit cube, k_eff = q_in. */
+dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy);
+
+/* ---- sizes and intermediate results (parity checks, debugging) ---- */
+
+/* n_nodes, n_tets, n_edges, nnz of L (with the diagonal), instances B. */
+dec_status dec_get_sizes(const dec_ctx* ctx, int64_t* n_nodes, int64_t* n_tets,
+                         int64_t* n_edges, int64_t* nnz, int32_t* n_instances);
+
+/* Edge list E [n_edges*2] int32 (i < j, sorted) and tet->edge map
+ * t2e [n_tets*6] int32; either may be NULL.  Host or device buffers. */
+dec_status dec_get_edges(dec_ctx* ctx, int32_t* E, int32_t* t2e);
+
+/* Hodge star *1 of the uncracked mesh w [n_edges] f64, and the first crack
+ * state per edge first_cut [n_edges] uint8 (n_scales, or 1 without scales,
+ * when never cut); either may be NULL.  Host or device buffers. */
+dec_status dec_get_hodge(dec_ctx* ctx, double* w, uint8_t* first_cut);
+
+/* CSR of L: rowptr [n_nodes+1] int32, col [nnz] int32, columns sorted,
+ * diagonal included.  val [nnz] f64 and b [n_nodes] f64 of instance
+ * `inst`.  Any pointer may be NULL.  Host or device buffers. */
+dec_status dec_get_csr(dec_ctx* ctx, int32_t inst, int32_t* rowptr,
+                       int32_t* col, double* val, double* b);
+
+/* FSAI factor in L's CSR layout, g [nnz] f64: entries with col <= row hold
+ * G[row][col], entries with col > row hold G[col][row] (the transpose).
+ * Jacobi: the diagonal holds 1/L_ii and off-diagonals 0.  Host or device. */
+dec_status dec_get_precond(dec_ctx* ctx, double* g);
+
+/* ---- measurement ---- */
+
+/* kernels that dec_time_kernel can time */
+enum {
+  DEC_KERNEL_SPMV_F64 = 0,   /* q = L p, FP64 values and vectors, fused p.q   */
+  DEC_KERNEL_SPMV_F32 = 1,   /* same with FP32 values and vectors             */
+  DEC_KERNEL_FSAI_F64 = 2,   /* z = G^T (G r), FP64 factor (two launches)     */
+  DEC_KERNEL_FSAI_BF16 = 3   /* same with the BF16 factor and FP32 vectors    */
+};
+
+/* Launch one solver kernel `reps` times on instance 0's matrix after a
+ * successful dec_laplacian_build, each launch timed alone with CUDA events
+ * on the context's stream and preceded, outside the timed interval, by a
+ * write of `flush_bytes` bytes of device memory (pass more than the L2 size
+ * to time the kernel with a cold cache).  *avg_ms receives the mean launch
+ * duration.  The launch configuration is the one dec_solve uses.  Allocates
+ * a flush buffer of `flush_bytes` owned by the context.  Overwrites the
+ * solver's scratch vectors (a later dec_k_eff is unaffected).
+ * Errors: DEC_ERR_STATE, DEC_ERR_ARG for an unknown kernel or reps < 1. */
+dec_status dec_time_kernel(dec_ctx* ctx, int32_t kernel, int32_t reps,
+                           int64_t flush_bytes, double* avg_ms);
+
+/* Number of CUDA kernels the context has launched since dec_create,
+ * counting every kernel node of each replayed CUDA graph. */
+dec_status dec_get_launch_count(const dec_ctx* ctx, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEC_GB300_H */

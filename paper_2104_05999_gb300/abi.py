@@ -1,0 +1,235 @@
+"""ctypes binding of the C ABI in ``include/dec.h`` (libdec_gb300.so).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays may be numpy arrays (host memory) or torch CUDA tensors
+(device memory of the context's GPU); they must be C-contiguous and of the
+dtype the C declaration names.  Every call raises ``DecError`` on a non-OK
+status.  Loading fails loudly when the compiled library is missing: there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._build import lib_path
+
+DEC_OK = 0
+DEC_ERR_ARG = 1
+DEC_ERR_MESH = 2
+DEC_ERR_CUDA = 3
+DEC_ERR_BREAKDOWN = 4
+DEC_NOT_CONVERGED = 5
+DEC_ERR_TIMEOUT = 6
+DEC_ERR_STATE = 7
+DEC_ERR_LIMIT = 8
+STATUS_NAMES = {
+    0: "DEC_OK", 1: "DEC_ERR_ARG", 2: "DEC_ERR_MESH", 3: "DEC_ERR_CUDA",
+    4: "DEC_ERR_BREAKDOWN", 5: "DEC_NOT_CONVERGED", 6: "DEC_ERR_TIMEOUT",
+    7: "DEC_ERR_STATE", 8: "DEC_ERR_LIMIT"}
+
+DEC_NODE_FREE, DEC_NODE_DIRICHLET, DEC_NODE_NEUMANN = 0, 1, 2
+DEC_PRECOND_JACOBI, DEC_PRECOND_FSAI = 0, 1
+DEC_MODE_FP64, DEC_MODE_MIXED = 0, 1
+DEC_KERNEL_SPMV_F64, DEC_KERNEL_SPMV_F32 = 0, 1
+DEC_KERNEL_FSAI_F64, DEC_KERNEL_FSAI_BF16 = 2, 3
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_I32 = C.c_int32
+_D = C.c_double
+
+# name -> (argtypes); all return dec_status (int)
+SIGNATURES = {
+    "dec_create": [C.POINTER(_P), C.c_int, _P],
+    "dec_destroy": [_P],
+    "dec_mesh_upload": [_P, _P, _I64, _P, _I64, _P],
+    "dec_hodge_assemble": [_P, _P, _P, _I64, _P, _I32],
+    "dec_laplacian_build": [_P, _P, _I32, _I32],
+    "dec_solve": [_P, _D, _I32, _I32, _P, _P, _P],
+    "dec_k_eff": [_P, _P, _P, _P],
+    "dec_get_sizes": [_P, _P, _P, _P, _P, _P],
+    "dec_get_edges": [_P, _P, _P],
+    "dec_get_hodge": [_P, _P, _P],
+    "dec_get_csr": [_P, _I32, _P, _P, _P, _P],
+    "dec_get_precond": [_P, _P],
+    "dec_time_kernel": [_P, _I32, _I32, _I64, _P],
+    "dec_get_launch_count": [_P, _P],
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the compiled library (once).  Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library {path} is not built; run "
+            "paper_2104_05999_gb300._build.build() first")
+    lib = C.CDLL(path)
+    for name, argt in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = argt
+        fn.restype = C.c_int
+    lib.dec_last_error.argtypes = [_P]
+    lib.dec_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class DecError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.message = message
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+
+
+def _ptr(a, dtype):
+    """Address of a contiguous numpy array / torch tensor of ``dtype``."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return a.ctypes.data
+    # torch tensor (host or device)
+    import torch
+    tdt = {np.float64: torch.float64, np.int32: torch.int32,
+           np.uint8: torch.uint8}[np.dtype(dtype).type]
+    if a.dtype != tdt or not a.is_contiguous():
+        raise TypeError(f"expected a contiguous {tdt} tensor")
+    return a.data_ptr()
+
+
+class Context:
+    """One dec_ctx: owns the device buffers of one mesh and its solves."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self.lib = load()
+        h = _P()
+        st = self.lib.dec_create(C.byref(h), int(device), stream)
+        if st != DEC_OK:
+            raise DecError(st, self.lib.dec_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != DEC_OK:
+            raise DecError(st, self.lib.dec_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dec_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- entry points -------------------------------------------------
+    def dec_mesh_upload(self, xyz, tets, node_tag):
+        n = len(xyz)
+        m = len(tets)
+        return self._check(self.lib.dec_mesh_upload(
+            self.h, _ptr(xyz, np.float64), n, _ptr(tets, np.int32), m,
+            _ptr(node_tag, np.uint8)))
+
+    def dec_hodge_assemble(self, k=None, discs=None, scales=None):
+        nd = 0 if discs is None else len(discs)
+        ns = 0 if scales is None else len(scales)
+        return self._check(self.lib.dec_hodge_assemble(
+            self.h, _ptr(k, np.float64), _ptr(discs, np.float64), nd,
+            _ptr(scales, np.float64), ns))
+
+    def dec_laplacian_build(self, T0, precond=DEC_PRECOND_FSAI):
+        n_sets = 1 if T0.ndim == 1 else T0.shape[0]
+        return self._check(self.lib.dec_laplacian_build(
+            self.h, _ptr(T0, np.float64), n_sets, int(precond)))
+
+    def dec_solve(self, rtol, max_iter=100000, mode=DEC_MODE_FP64, T_out=None,
+                  raise_on_error=True):
+        """Returns (status, iters[B], relres[B])."""
+        B = self.sizes()[4]
+        iters = np.zeros(B, dtype=np.int32)
+        relres = np.zeros(B, dtype=np.float64)
+        st = self.lib.dec_solve(self.h, float(rtol), int(max_iter), int(mode),
+                                _ptr(T_out, np.float64), iters.ctypes.data,
+                                relres.ctypes.data)
+        if raise_on_error:
+            self._check(st)
+        return st, iters, relres
+
+    def dec_k_eff(self):
+        B = self.sizes()[4]
+        q_in = np.zeros(B)
+        q_out = np.zeros(B)
+        energy = np.zeros(B)
+        self._check(self.lib.dec_k_eff(self.h, q_in.ctypes.data,
+                                       q_out.ctypes.data, energy.ctypes.data))
+        return q_in, q_out, energy
+
+    # ---- getters --------------------------------------------------------
+    def sizes(self):
+        v = [C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()]
+        b = C.c_int32()
+        self._check(self.lib.dec_get_sizes(self.h, *[C.byref(x) for x in v],
+                                           C.byref(b)))
+        return tuple(x.value for x in v) + (b.value,)
+
+    def dec_get_edges(self):
+        n, m, ne, nnz, B = self.sizes()
+        E = np.zeros((ne, 2), dtype=np.int32)
+        t2e = np.zeros((m, 6), dtype=np.int32)
+        self._check(self.lib.dec_get_edges(self.h, E.ctypes.data, t2e.ctypes.data))
+        return E, t2e
+
+    def dec_get_hodge(self):
+        n, m, ne, nnz, B = self.sizes()
+        w = np.zeros(ne)
+        fc = np.zeros(ne, dtype=np.uint8)
+        self._check(self.lib.dec_get_hodge(self.h, w.ctypes.data, fc.ctypes.data))
+        return w, fc
+
+    def dec_get_csr(self, inst=0, values=True):
+        n, m, ne, nnz, B = self.sizes()
+        rowptr = np.zeros(n + 1, dtype=np.int32)
+        col = np.zeros(nnz, dtype=np.int32)
+        val = np.zeros(nnz) if values else None
+        b = np.zeros(n) if values else None
+        self._check(self.lib.dec_get_csr(
+            self.h, int(inst), rowptr.ctypes.data, col.ctypes.data,
+            None if val is None else val.ctypes.data,
+            None if b is None else b.ctypes.data))
+        return rowptr, col, val, b
+
+    def dec_get_precond(self):
+        nnz = self.sizes()[3]
+        g = np.zeros(nnz)
+        self._check(self.lib.dec_get_precond(self.h, g.ctypes.data))
+        return g
+
+    def dec_get_launch_count(self):
+        c = C.c_int64()
+        self._check(self.lib.dec_get_launch_count(self.h, C.byref(c)))
+        return c.value
+
+    def dec_time_kernel(self, kernel, reps=20, flush_bytes=512 << 20):
+        """Mean duration (ms) of one launch of a solver kernel, cold L2."""
+        ms = C.c_double()
+        self._check(self.lib.dec_time_kernel(self.h, int(kernel), int(reps),
+                                             int(flush_bytes), C.byref(ms)))
+        return ms.value

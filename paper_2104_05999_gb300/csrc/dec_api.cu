@@ -1,0 +1,387 @@
+// dec_api.cu - the C ABI entry points declared in include/dec.h: argument
+// checks, host<->device copies and the order of the internal launches.
+#include "dec_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using dec::DevBuf;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// copy `count` elements from a host or device pointer into a context buffer
+template <typename T>
+cudaError_t upload(DevBuf<T>& dst, const T* src, int64_t count, cudaStream_t s) {
+  cudaError_t e = dst.ensure(count);
+  if (e != cudaSuccess) return e;
+  if (count == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst.p, src, sizeof(T) * count, cudaMemcpyDefault, s);
+}
+
+template <typename T>
+cudaError_t download(T* dst, const T* src, int64_t count, cudaStream_t s) {
+  if (!dst || count == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyDefault, s);
+}
+
+// host copy of a host-or-device array (for argument checks of small inputs)
+template <typename T>
+cudaError_t host_copy(std::vector<T>& out, const T* src, int64_t count, cudaStream_t s) {
+  out.resize(count);
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(out.data(), src, sizeof(T) * count,
+                                  cudaMemcpyDefault, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+dec_status set_device(dec_ctx* ctx) {
+  DEC_TRY(cudaSetDevice(ctx->device));
+  return DEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dec_status dec_create(dec_ctx** out, int device, void* stream) {
+  if (!out) {
+    g_create_error = "dec_create: ctx is NULL";
+    return DEC_ERR_ARG;
+  }
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || device < 0 || device >= count) {
+    g_create_error = std::string("dec_create: no CUDA device ") + std::to_string(device) +
+                     (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : "");
+    return e != cudaSuccess ? DEC_ERR_CUDA : DEC_ERR_ARG;
+  }
+  dec_ctx* ctx = new (std::nothrow) dec_ctx();
+  if (!ctx) {
+    g_create_error = "dec_create: out of host memory";
+    return DEC_ERR_ARG;
+  }
+  ctx->device = device;
+  e = cudaSetDevice(device);
+  if (e == cudaSuccess) {
+    if (stream) {
+      ctx->stream = (cudaStream_t)stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      ctx->own_stream = true;
+    }
+  }
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) {
+    ctx->reduce_grid = ctx->num_sms * 4;
+    e = ctx->partial.ensure((size_t)dec::kRedSlots * ctx->reduce_grid);
+  }
+  if (e == cudaSuccess) e = ctx->ticket.ensure(1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ticket.p, 0, sizeof(unsigned), ctx->stream);
+  if (e == cudaSuccess) e = ctx->cg.ensure(1);
+  if (e == cudaSuccess) e = ctx->errflag.ensure(4);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("dec_create: ") + cudaGetErrorString(e);
+    dec_destroy(ctx);
+    return DEC_ERR_CUDA;
+  }
+  *out = ctx;
+  return DEC_OK;
+}
+
+dec_status dec_destroy(dec_ctx* ctx) {
+  if (!ctx) return DEC_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->release_all();
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return DEC_OK;
+}
+
+const char* dec_last_error(const dec_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+dec_status dec_mesh_upload(dec_ctx* ctx, const double* xyz, int64_t n_nodes,
+                           const int32_t* tets, int64_t n_tets,
+                           const uint8_t* node_tag) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (!xyz || !tets || !node_tag)
+    return ctx->fail(DEC_ERR_ARG, "mesh_upload: NULL pointer");
+  if (n_nodes < 4 || n_nodes >= INT32_MAX)
+    return ctx->fail(DEC_ERR_ARG, "mesh_upload: n_nodes must be in [4, 2^31-1)");
+  if (n_tets < 1 || 6 * n_tets >= ((int64_t)1 << 32))
+    return ctx->fail(DEC_ERR_ARG, "mesh_upload: n_tets must be in [1, 2^32/6)");
+  DEC_TRY_STATUS(set_device(ctx));
+  ctx->stage = 0;
+  ctx->n = n_nodes;
+  ctx->m = n_tets;
+  cudaStream_t s = ctx->stream;
+  DEC_TRY(upload(ctx->xyz, xyz, 3 * n_nodes, s));
+  DEC_TRY(upload(ctx->tets, tets, 4 * n_tets, s));
+  DEC_TRY(upload(ctx->tag, node_tag, n_nodes, s));
+  DEC_TRY_STATUS(dec::validate_mesh(ctx));
+  DEC_TRY_STATUS(dec::build_edges(ctx));
+  DEC_TRY_STATUS(dec::build_csr_structure(ctx));
+  DEC_TRY(cudaStreamSynchronize(s));
+  ctx->stage = 1;
+  return DEC_OK;
+}
+
+dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k, const double* discs,
+                              int64_t n_discs, const double* scales,
+                              int32_t n_scales) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 1) return ctx->fail(DEC_ERR_STATE, "hodge_assemble: no mesh uploaded");
+  if (n_discs < 0 || (n_discs > 0 && !discs))
+    return ctx->fail(DEC_ERR_ARG, "hodge_assemble: bad discs / n_discs");
+  if (n_discs >= INT32_MAX) return ctx->fail(DEC_ERR_LIMIT, "hodge_assemble: too many discs");
+  if (scales && (n_scales < 1 || n_scales > 255))
+    return ctx->fail(DEC_ERR_ARG, "hodge_assemble: n_scales must be in [1, 255]");
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  ctx->stage = 1;
+  // conductivity: finite and > 0
+  const bool has_k = k != nullptr;
+  if (has_k) {
+    std::vector<double> hk;
+    DEC_TRY(host_copy(hk, k, ctx->m, s));
+    for (double v : hk)
+      if (!(v > 0.0) || !std::isfinite(v))
+        return ctx->fail(DEC_ERR_ARG, "hodge_assemble: conductivity must be finite and > 0");
+    DEC_TRY(upload(ctx->kcond, hk.data(), ctx->m, s));
+  }
+  std::vector<double> hs;
+  if (scales) {
+    DEC_TRY(host_copy(hs, scales, n_scales, s));
+    for (int i = 0; i < n_scales; ++i)
+      if (!(hs[i] > 0.0) || !std::isfinite(hs[i]) || (i > 0 && !(hs[i] > hs[i - 1])))
+        return ctx->fail(DEC_ERR_ARG, "hodge_assemble: scales must be finite, > 0, increasing");
+  } else {
+    hs.assign(1, 1.0);
+  }
+  ctx->n_scales = (int)hs.size();
+  DEC_TRY(upload(ctx->scales, hs.data(), (int64_t)hs.size(), s));
+  if (n_discs > 0) {
+    std::vector<double> hd;
+    DEC_TRY(host_copy(hd, discs, 7 * n_discs, s));
+    for (int64_t i = 0; i < n_discs; ++i) {
+      const double* d = &hd[7 * i];
+      bool ok = true;
+      for (int j = 0; j < 7; ++j) ok = ok && std::isfinite(d[j]);
+      const double nn = d[3] * d[3] + d[4] * d[4] + d[5] * d[5];
+      if (!ok || !(d[6] > 0.0) || std::fabs(nn - 1.0) > 1e-9)
+        return ctx->fail(DEC_ERR_ARG, "hodge_assemble: a disc needs a finite centre, unit normal and r > 0");
+    }
+    DEC_TRY(upload(ctx->discs, hd.data(), 7 * n_discs, s));
+  }
+  DEC_TRY_STATUS(dec::assemble_hodge(ctx, n_discs, has_k));
+  DEC_TRY(cudaStreamSynchronize(s));
+  ctx->stage = 2;
+  return DEC_OK;
+}
+
+dec_status dec_laplacian_build(dec_ctx* ctx, const double* T0, int32_t n_sets,
+                               int32_t precond) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 2) return ctx->fail(DEC_ERR_STATE, "laplacian_build: no Hodge star assembled");
+  if (!T0 || n_sets < 1) return ctx->fail(DEC_ERR_ARG, "laplacian_build: bad T0 / n_sets");
+  if (precond != DEC_PRECOND_JACOBI && precond != DEC_PRECOND_FSAI)
+    return ctx->fail(DEC_ERR_ARG, "laplacian_build: unknown preconditioner");
+  if (ctx->n_scales > 1 && n_sets > 1)
+    return ctx->fail(DEC_ERR_ARG, "laplacian_build: crack states and several T0 sets at once");
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  ctx->stage = 2;
+  const int64_t n = ctx->n, nnz = ctx->nnz;
+  ctx->n_sets = n_sets;
+  ctx->precond = precond;
+  ctx->B = std::max(ctx->n_scales, n_sets);
+  const int V = ctx->n_scales;  // value sets
+  DEC_TRY(upload(ctx->T0, T0, (int64_t)n_sets * n, s));
+  DEC_TRY(ctx->val64.ensure((size_t)V * nnz));
+  DEC_TRY(ctx->val32.ensure((size_t)V * nnz));
+  DEC_TRY(ctx->b.ensure((size_t)ctx->B * n));
+  if (precond == DEC_PRECOND_FSAI) {
+    DEC_TRY(ctx->g64.ensure((size_t)V * nnz));
+    DEC_TRY(ctx->g16.ensure((size_t)V * nnz));
+  } else {
+    DEC_TRY(ctx->dinv64.ensure((size_t)V * n));
+    DEC_TRY(ctx->dinv32.ensure((size_t)V * n));
+  }
+  for (int inst = 0; inst < ctx->B; ++inst)
+    DEC_TRY_STATUS(dec::build_values(ctx, inst, true));
+  for (int vs = 0; vs < V; ++vs) DEC_TRY_STATUS(dec::build_precond(ctx, vs, true));
+  DEC_TRY(cudaStreamSynchronize(s));
+  ctx->stage = 3;
+  return DEC_OK;
+}
+
+dec_status dec_solve(dec_ctx* ctx, double rtol, int32_t max_iter, int32_t mode,
+                     double* T_out, int32_t* iters, double* relres) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 3) return ctx->fail(DEC_ERR_STATE, "solve: no Laplacian built");
+  if (!(rtol > 0.0) || !std::isfinite(rtol) || max_iter < 1)
+    return ctx->fail(DEC_ERR_ARG, "solve: rtol must be > 0 and max_iter >= 1");
+  if (mode != DEC_MODE_FP64 && mode != DEC_MODE_MIXED)
+    return ctx->fail(DEC_ERR_ARG, "solve: unknown mode");
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  ctx->stage = 3;
+  DEC_TRY(ctx->u.ensure((size_t)ctx->B * n));
+  DEC_TRY(ctx->out3.ensure(3 * (size_t)ctx->B + 1));
+  if (mode == DEC_MODE_FP64) {
+    for (auto* bf : {&ctx->x64, &ctx->r64, &ctx->z64, &ctx->p64, &ctx->q64, &ctx->t64})
+      DEC_TRY(bf->ensure(n));
+  } else {
+    for (auto* bf : {&ctx->x64, &ctx->r64, &ctx->t64}) DEC_TRY(bf->ensure(n));
+    for (auto* bf : {&ctx->x32, &ctx->r32, &ctx->z32, &ctx->p32, &ctx->q32, &ctx->t32})
+      DEC_TRY(bf->ensure(n));
+  }
+  ctx->iters_host.assign(ctx->B, 0);
+  ctx->relres_host.assign(ctx->B, 0.0);
+  dec_status worst = DEC_OK;
+  for (int inst = 0; inst < ctx->B; ++inst) {
+    dec_status st = dec::solve_instance(ctx, inst, rtol, max_iter, mode,
+                                        &ctx->iters_host[inst], &ctx->relres_host[inst]);
+    if (st == DEC_ERR_CUDA) return st;
+    if (st != DEC_OK && worst == DEC_OK) worst = st;
+  }
+  std::string keep = ctx->err;
+  if (T_out) {
+    for (int inst = 0; inst < ctx->B; ++inst) {
+      DEC_TRY_STATUS(dec::form_T(ctx, inst, ctx->t64.p));
+      DEC_TRY(download(T_out + (int64_t)inst * n, (const double*)ctx->t64.p, n, s));
+    }
+  }
+  DEC_TRY(cudaStreamSynchronize(s));
+  if (iters) std::copy(ctx->iters_host.begin(), ctx->iters_host.end(), iters);
+  if (relres) std::copy(ctx->relres_host.begin(), ctx->relres_host.end(), relres);
+  ctx->err = keep;
+  ctx->stage = 4;
+  return worst;
+}
+
+dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 4) return ctx->fail(DEC_ERR_STATE, "k_eff: no solution");
+  if (!q_in) return ctx->fail(DEC_ERR_ARG, "k_eff: q_in is NULL");
+  DEC_TRY_STATUS(set_device(ctx));
+  DEC_TRY(ctx->t64.ensure(ctx->n));
+  for (int inst = 0; inst < ctx->B; ++inst) {
+    double o[3];
+    DEC_TRY_STATUS(dec::k_eff_instance(ctx, inst, o));
+    q_in[inst] = o[0];
+    if (q_out) q_out[inst] = o[1];
+    if (energy) energy[inst] = o[2];
+  }
+  return DEC_OK;
+}
+
+dec_status dec_get_sizes(const dec_ctx* ctx, int64_t* n_nodes, int64_t* n_tets,
+                         int64_t* n_edges, int64_t* nnz, int32_t* n_instances) {
+  if (!ctx) return DEC_ERR_ARG;
+  if (n_nodes) *n_nodes = ctx->n;
+  if (n_tets) *n_tets = ctx->m;
+  if (n_edges) *n_edges = ctx->ne;
+  if (nnz) *nnz = ctx->nnz;
+  if (n_instances) *n_instances = ctx->B;
+  return DEC_OK;
+}
+
+dec_status dec_get_edges(dec_ctx* ctx, int32_t* E, int32_t* t2e) {
+  if (!ctx) return DEC_ERR_ARG;
+  if (ctx->stage < 1) return ctx->fail(DEC_ERR_STATE, "get_edges: no mesh");
+  DEC_TRY_STATUS(set_device(ctx));
+  DEC_TRY(download(E, (const int32_t*)ctx->E.p, 2 * ctx->ne, ctx->stream));
+  DEC_TRY(download(t2e, (const int32_t*)ctx->t2e.p, 6 * ctx->m, ctx->stream));
+  DEC_TRY(cudaStreamSynchronize(ctx->stream));
+  return DEC_OK;
+}
+
+dec_status dec_get_hodge(dec_ctx* ctx, double* w, uint8_t* first_cut) {
+  if (!ctx) return DEC_ERR_ARG;
+  if (ctx->stage < 2) return ctx->fail(DEC_ERR_STATE, "get_hodge: no Hodge star");
+  DEC_TRY_STATUS(set_device(ctx));
+  DEC_TRY(download(w, (const double*)ctx->w.p, ctx->ne, ctx->stream));
+  DEC_TRY(download(first_cut, (const uint8_t*)ctx->first_cut.p, ctx->ne, ctx->stream));
+  DEC_TRY(cudaStreamSynchronize(ctx->stream));
+  return DEC_OK;
+}
+
+dec_status dec_get_csr(dec_ctx* ctx, int32_t inst, int32_t* rowptr, int32_t* col,
+                       double* val, double* b) {
+  if (!ctx) return DEC_ERR_ARG;
+  if (ctx->stage < 1) return ctx->fail(DEC_ERR_STATE, "get_csr: no mesh");
+  if ((val || b) && ctx->stage < 3) return ctx->fail(DEC_ERR_STATE, "get_csr: no Laplacian");
+  if ((val || b) && (inst < 0 || inst >= ctx->B)) return ctx->fail(DEC_ERR_ARG, "get_csr: bad instance");
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  DEC_TRY(download(rowptr, (const int32_t*)ctx->rowptr.p, ctx->n + 1, s));
+  DEC_TRY(download(col, (const int32_t*)ctx->col.p, ctx->nnz, s));
+  const int vs = ctx->n_scales > 1 ? inst : 0;
+  if (val) DEC_TRY(download(val, (const double*)ctx->val64.p + (int64_t)vs * ctx->nnz, ctx->nnz, s));
+  if (b) DEC_TRY(download(b, (const double*)ctx->b.p + (int64_t)inst * ctx->n, ctx->n, s));
+  DEC_TRY(cudaStreamSynchronize(s));
+  return DEC_OK;
+}
+
+dec_status dec_get_precond(dec_ctx* ctx, double* g) {
+  if (!ctx) return DEC_ERR_ARG;
+  if (ctx->stage < 3) return ctx->fail(DEC_ERR_STATE, "get_precond: no Laplacian");
+  if (!g) return DEC_OK;
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  if (ctx->precond == DEC_PRECOND_FSAI) {
+    DEC_TRY(download(g, (const double*)ctx->g64.p, ctx->nnz, s));
+  } else {
+    // Jacobi: 1/L_ii on the diagonal slots, 0 elsewhere
+    std::vector<double> dinv(ctx->n);
+    std::vector<int32_t> dpos(ctx->n);
+    DEC_TRY(cudaMemcpyAsync(dinv.data(), ctx->dinv64.p, sizeof(double) * ctx->n,
+                            cudaMemcpyDeviceToHost, s));
+    DEC_TRY(cudaMemcpyAsync(dpos.data(), ctx->dpos.p, sizeof(int32_t) * ctx->n,
+                            cudaMemcpyDeviceToHost, s));
+    DEC_TRY(cudaStreamSynchronize(s));
+    std::vector<double> full(ctx->nnz, 0.0);
+    for (int64_t i = 0; i < ctx->n; ++i) full[dpos[i]] = dinv[i];
+    DEC_TRY(cudaMemcpyAsync(g, full.data(), sizeof(double) * ctx->nnz, cudaMemcpyDefault, s));
+  }
+  DEC_TRY(cudaStreamSynchronize(s));
+  return DEC_OK;
+}
+
+dec_status dec_time_kernel(dec_ctx* ctx, int32_t kernel, int32_t reps,
+                           int64_t flush_bytes, double* avg_ms) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 3) return ctx->fail(DEC_ERR_STATE, "time_kernel: no Laplacian built");
+  if (reps < 1 || flush_bytes < 0 || !avg_ms) return ctx->fail(DEC_ERR_ARG, "time_kernel: bad arguments");
+  if ((kernel == DEC_KERNEL_FSAI_F64 || kernel == DEC_KERNEL_FSAI_BF16) &&
+      ctx->precond != DEC_PRECOND_FSAI)
+    return ctx->fail(DEC_ERR_STATE, "time_kernel: no FSAI factor built");
+  DEC_TRY_STATUS(set_device(ctx));
+  return dec::time_kernel(ctx, kernel, reps, (size_t)flush_bytes, avg_ms);
+}
+
+dec_status dec_get_launch_count(const dec_ctx* ctx, int64_t* count) {
+  if (!ctx || !count) return DEC_ERR_ARG;
+  *count = ctx->launches;
+  return DEC_OK;
+}
+
+}  // extern "C"

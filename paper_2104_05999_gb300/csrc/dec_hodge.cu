@@ -1,0 +1,356 @@
+// dec_hodge.cu - the diagonal Hodge star *1 on primal edges from the
+// circumcentric dual (Sec. 2.1: ratio of dual to primal volumes), with the
+// conductivity of each tet scaling its share (Sec. 2.1) and penny cracks
+// making cut dual faces insulating (Sec. 2.5).
+//
+// One thread per tet computes, in FP64, its circumcentre, the circumcentres
+// and inward unit normals of its 4 faces, and for each of its 6 edges the
+// signed area of the dual-face piece inside the tet:
+//   piece = k_T * sum over the 2 faces F of the tet that contain e of
+//           (1/2) * h1(F) * h2(F),
+//   h1 = signed distance, inside F, from the edge midpoint to c_F
+//        (+ towards F's third vertex),
+//   h2 = signed distance from c_T to the plane of F (+ towards the tet's
+//        fourth vertex).
+// Each half (m_e, c_F, c_T) is a right triangle in the bisector plane of e;
+// the crack test runs on exactly these triangles.  A second pass sums the
+// pieces of every edge in a fixed order (sorted tet*6+slot), so *1 is
+// deterministic without atomics.
+#include "dec_internal.cuh"
+
+#include <math_constants.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace dec {
+
+struct V3 {
+  double x, y, z;
+};
+__device__ __forceinline__ V3 mk(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// circumcentre of triangle (p, p+a, p+b): p + ((|a|^2 b - |b|^2 a) x (a x b)) / (2 |a x b|^2)
+__device__ __forceinline__ V3 tri_circumcentre(V3 p, V3 q, V3 r) {
+  V3 a = q - p, b = r - p;
+  V3 axb = cross(a, b);
+  V3 num = cross(dot(a, a) * b - dot(b, b) * a, axb);
+  return p + (0.5 / dot(axb, axb)) * num;
+}
+
+// Distance, in the disc's plane, from the disc centre to the segment where
+// the plane meets the closed triangle (P0, P1, P2); +inf when the plane misses
+// the triangle or contains it.
+__device__ double crack_rho(V3 P0, V3 P1, V3 P2, V3 c, V3 nrm) {
+  V3 P[3] = {P0, P1, P2};
+  double s[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s[i] = dot(P[i] - c, nrm);
+  int count = 0;
+  V3 A = mk(0, 0, 0), B = mk(0, 0, 0);
+  const int ei[3] = {0, 1, 0}, ej[3] = {1, 2, 2};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double si = s[ei[k]], sj = s[ej[k]];
+    if (si * sj < 0.0) {
+      double t = si / (si - sj);
+      V3 X = P[ei[k]] + t * (P[ej[k]] - P[ei[k]]);
+      if (count == 0) A = X; else if (count == 1) B = X;
+      ++count;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (s[i] == 0.0) {
+      if (count == 0) A = P[i]; else if (count == 1) B = P[i];
+      ++count;
+    }
+  }
+  if (count == 0 || count >= 3) return CUDART_INF;
+  if (count == 1) B = A;
+  V3 d = B - A;
+  double dd = dot(d, d);
+  double tt = 0.0;
+  if (dd > 0.0) tt = fmin(fmax(dot(c - A, d) / dd, 0.0), 1.0);
+  V3 cl = A + tt * d;
+  V3 g = c - cl;
+  return sqrt(dot(g, g));
+}
+
+struct DiscGrid {
+  double lo[3];
+  double inv_cell;
+  int dim[3];
+  const int32_t* start;   // [cells+1]
+  const int32_t* items;   // disc ids
+  const double* discs;    // [nd][7]
+  const double* scales;   // [n_states]
+  int n_states;
+  int nd;
+};
+
+__constant__ int kEdgeA[6] = {0, 0, 0, 1, 1, 2};
+__constant__ int kEdgeB[6] = {1, 2, 3, 2, 3, 3};
+__constant__ int kEdgeC[6] = {2, 1, 1, 0, 0, 0};  // the two other vertices
+__constant__ int kEdgeD[6] = {3, 3, 2, 3, 2, 1};
+
+__global__ void __launch_bounds__(128)
+hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
+                 const double* __restrict__ kcond, int64_t m,
+                 double* __restrict__ piece, uint8_t* __restrict__ slot_cut,
+                 DiscGrid grid) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int4 v4 = reinterpret_cast<const int4*>(tets)[t];
+    const int vid[4] = {v4.x, v4.y, v4.z, v4.w};
+    V3 X[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      X[i] = mk(xyz[3 * (int64_t)vid[i]], xyz[3 * (int64_t)vid[i] + 1],
+                xyz[3 * (int64_t)vid[i] + 2]);
+    const double kT = kcond ? kcond[t] : 1.0;
+    // tet circumcentre: x0 + (|a|^2 (b x c) + |b|^2 (c x a) + |c|^2 (a x b)) / (2 a.(b x c))
+    V3 a = X[1] - X[0], b = X[2] - X[0], c = X[3] - X[0];
+    V3 bxc = cross(b, c), cxa = cross(c, a), axb = cross(a, b);
+    double det6 = dot(a, bxc);
+    V3 cT = X[0] + (0.5 / det6) * (dot(a, a) * bxc + dot(b, b) * cxa + dot(c, c) * axb);
+    // face opposite vertex v: circumcentre and unit normal pointing to v
+    V3 cF[4], nin[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i0 = (v + 1) & 3, i1 = (v + 2) & 3, i2 = (v + 3) & 3;
+      cF[v] = tri_circumcentre(X[i0], X[i1], X[i2]);
+      V3 nn = cross(X[i1] - X[i0], X[i2] - X[i0]);
+      double s = dot(nn, X[v] - X[i0]) > 0.0 ? 1.0 : -1.0;
+      nin[v] = (s / sqrt(dot(nn, nn))) * nn;
+    }
+    uint8_t first[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      const int ea = kEdgeA[s], eb = kEdgeB[s], ec = kEdgeC[s], ed = kEdgeD[s];
+      V3 me = 0.5 * (X[ea] + X[eb]);
+      V3 e = X[eb] - X[ea];
+      double ee = dot(e, e);
+      double area = 0.0;
+      // face {a,b,c} is opposite d (third vertex c); face {a,b,d} opposite c
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int third = h == 0 ? ec : ed;
+        const int opp = h == 0 ? ed : ec;
+        V3 w = X[third] - me;
+        V3 tv = w - (dot(w, e) / ee) * e;          // in F, normal to e
+        double h1 = dot(cF[opp] - me, tv) / sqrt(dot(tv, tv));
+        double h2 = dot(cT - cF[opp], nin[opp]);
+        area += 0.5 * h1 * h2;
+      }
+      piece[t * 6 + s] = kT * area;
+      first[s] = (uint8_t)grid.n_states;
+    }
+    if (grid.nd > 0) {
+      // bounding box of the 12 dual sub-triangles of the tet
+      double lo[3], hi[3];
+      lo[0] = hi[0] = cT.x; lo[1] = hi[1] = cT.y; lo[2] = hi[2] = cT.z;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        lo[0] = fmin(lo[0], fmin(cF[v].x, X[v].x)); hi[0] = fmax(hi[0], fmax(cF[v].x, X[v].x));
+        lo[1] = fmin(lo[1], fmin(cF[v].y, X[v].y)); hi[1] = fmax(hi[1], fmax(cF[v].y, X[v].y));
+        lo[2] = fmin(lo[2], fmin(cF[v].z, X[v].z)); hi[2] = fmax(hi[2], fmax(cF[v].z, X[v].z));
+      }
+      int c0[3], c1[3];
+      bool empty = false;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double f0 = (lo[d] - grid.lo[d]) * grid.inv_cell;
+        double f1 = (hi[d] - grid.lo[d]) * grid.inv_cell;
+        if (f1 < 0.0 || f0 >= (double)grid.dim[d]) empty = true;
+        c0[d] = (int)fmax(0.0, floor(f0));
+        c1[d] = (int)fmin((double)grid.dim[d] - 1.0, floor(f1));
+      }
+      auto test_disc = [&](int id) {
+        const double* dsc = grid.discs + 7 * (int64_t)id;
+        V3 dc = mk(dsc[0], dsc[1], dsc[2]);
+        V3 dn = mk(dsc[3], dsc[4], dsc[5]);
+        const double r = dsc[6];
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+          if (first[s] == 0) continue;
+          V3 me = 0.5 * (X[kEdgeA[s]] + X[kEdgeB[s]]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int opp = h == 0 ? kEdgeD[s] : kEdgeC[s];
+            double rho = crack_rho(me, cF[opp], cT, dc, dn);
+            for (int st = 0; st < (int)first[s]; ++st)
+              if (rho <= grid.scales[st] * r) {
+                first[s] = (uint8_t)st;
+                break;
+              }
+          }
+        }
+      };
+      if (!empty) {
+        const int64_t ncell = (int64_t)(c1[0] - c0[0] + 1) * (c1[1] - c0[1] + 1) *
+                              (c1[2] - c0[2] + 1);
+        if (ncell > grid.nd) {
+          // a far circumcentre (flat boundary tet): fewer tests without the grid
+          for (int id = 0; id < grid.nd; ++id) test_disc(id);
+        } else {
+          for (int gz = c0[2]; gz <= c1[2]; ++gz)
+            for (int gy = c0[1]; gy <= c1[1]; ++gy)
+              for (int gx = c0[0]; gx <= c1[0]; ++gx) {
+                const int cell = gx + grid.dim[0] * (gy + grid.dim[1] * gz);
+                for (int it = grid.start[cell]; it < grid.start[cell + 1]; ++it)
+                  test_disc(grid.items[it]);
+              }
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 6; ++s) slot_cut[t * 6 + s] = first[s];
+  }
+}
+
+// *1[e] = (sum of the pieces of e, in increasing tet*6+slot) / |e|;
+// first_cut[e] = min over those slots.
+__global__ void edge_reduce_kernel(const int32_t* __restrict__ E,
+                                   const double* __restrict__ xyz,
+                                   const int32_t* __restrict__ seg_start,
+                                   const uint32_t* __restrict__ seg_pay,
+                                   const double* __restrict__ piece,
+                                   const uint8_t* __restrict__ slot_cut,
+                                   int64_t ne, double* __restrict__ w,
+                                   uint8_t* __restrict__ first_cut) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double sum = 0.0;
+    unsigned fc = 255u;
+    for (int32_t k = seg_start[e]; k < seg_start[e + 1]; ++k) {
+      uint32_t p = seg_pay[k];
+      sum += piece[p];
+      fc = min(fc, (unsigned)slot_cut[p]);
+    }
+    int2 ij = reinterpret_cast<const int2*>(E)[e];
+    double dx = xyz[3 * (int64_t)ij.y] - xyz[3 * (int64_t)ij.x];
+    double dy = xyz[3 * (int64_t)ij.y + 1] - xyz[3 * (int64_t)ij.x + 1];
+    double dz = xyz[3 * (int64_t)ij.y + 2] - xyz[3 * (int64_t)ij.x + 2];
+    w[e] = sum / sqrt(dx * dx + dy * dy + dz * dz);
+    first_cut[e] = (uint8_t)fc;
+  }
+}
+
+// uniform grid of disc bounding boxes (radius scaled by the largest state)
+__global__ void disc_bin_kernel(const double* __restrict__ discs, int nd,
+                                double smax, DiscGrid g, int32_t* __restrict__ counts,
+                                int32_t* __restrict__ cursor,
+                                int32_t* __restrict__ items, int fill) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd;
+       i += gridDim.x * blockDim.x) {
+    const double* d = discs + 7 * (int64_t)i;
+    const double R = d[6] * smax;
+    int c0[3], c1[3];
+    for (int k = 0; k < 3; ++k) {
+      c0[k] = max(0, (int)floor((d[k] - R - g.lo[k]) * g.inv_cell));
+      c1[k] = min(g.dim[k] - 1, (int)floor((d[k] + R - g.lo[k]) * g.inv_cell));
+    }
+    for (int z = c0[2]; z <= c1[2]; ++z)
+      for (int y = c0[1]; y <= c1[1]; ++y)
+        for (int x = c0[0]; x <= c1[0]; ++x) {
+          int cell = x + g.dim[0] * (y + g.dim[1] * z);
+          if (!fill) atomicAdd(&counts[cell], 1);
+          else items[atomicAdd(&cursor[cell], 1)] = i;
+        }
+  }
+}
+
+__global__ void copy_i32_kernel(const int32_t* a, int32_t* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k) {
+  cudaStream_t s = ctx->stream;
+  const int64_t m = ctx->m, q = 6 * m;
+  DEC_TRY(ctx->piece.ensure(q));
+  DEC_TRY(ctx->slot_cut.ensure(q));
+  DEC_TRY(ctx->w.ensure(ctx->ne));
+  DEC_TRY(ctx->first_cut.ensure(ctx->ne));
+  DiscGrid g{};
+  g.nd = (int)nd;
+  g.n_states = ctx->n_scales;
+  g.discs = ctx->discs.p;
+  g.scales = ctx->scales.p;
+  if (nd > 0) {
+    // grid bounds from a host copy of the discs
+    std::vector<double> hd(7 * nd), hs(ctx->n_scales);
+    DEC_TRY(cudaMemcpyAsync(hd.data(), ctx->discs.p, sizeof(double) * 7 * nd,
+                            cudaMemcpyDeviceToHost, s));
+    DEC_TRY(cudaMemcpyAsync(hs.data(), ctx->scales.p, sizeof(double) * ctx->n_scales,
+                            cudaMemcpyDeviceToHost, s));
+    DEC_TRY(cudaStreamSynchronize(s));
+    const double smax = hs.back();
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, rmax = 0;
+    for (int64_t i = 0; i < nd; ++i) {
+      const double R = hd[7 * i + 6] * smax;
+      rmax = std::max(rmax, R);
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], hd[7 * i + k] - R);
+        hi[k] = std::max(hi[k], hd[7 * i + k] + R);
+      }
+    }
+    double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    double cell = std::max(2.0 * rmax, ext / 128.0);
+    for (int k = 0; k < 3; ++k) {
+      g.lo[k] = lo[k];
+      g.dim[k] = std::max(1, (int)std::ceil((hi[k] - lo[k]) / cell));
+    }
+    g.inv_cell = 1.0 / cell;
+    const int64_t cells = (int64_t)g.dim[0] * g.dim[1] * g.dim[2];
+    DEC_TRY(ctx->grid_start.ensure(2 * (cells + 1)));
+    int32_t* counts = ctx->grid_start.p;             // [cells+1] -> starts
+    int32_t* cursor = ctx->grid_start.p + cells + 1;  // fill cursors
+    DEC_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (cells + 1), s));
+    disc_bin_kernel<<<(unsigned)((nd + 127) / 128), 128, 0, s>>>(
+        ctx->discs.p, (int)nd, smax, g, counts, cursor, nullptr, 0);
+    DEC_TRY(cudaGetLastError());
+    DEC_TRY(ctx->scan_tmp.ensure(scan_tmp_size(cells + 1)));
+    DEC_TRY(exclusive_scan_u32((const uint32_t*)counts, (uint32_t*)counts, cells + 1,
+                               ctx->scan_tmp.p, ctx->scan_tmp.cap, s));
+    int32_t total = 0;
+    DEC_TRY(cudaMemcpyAsync(&total, counts + cells, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+    DEC_TRY(cudaStreamSynchronize(s));
+    DEC_TRY(ctx->grid_items.ensure(total > 0 ? total : 1));
+    copy_i32_kernel<<<(unsigned)std::min<int64_t>((cells + 256) / 256, 4096), 256, 0, s>>>(
+        counts, cursor, cells + 1);
+    disc_bin_kernel<<<(unsigned)((nd + 127) / 128), 128, 0, s>>>(
+        ctx->discs.p, (int)nd, smax, g, counts, cursor, ctx->grid_items.p, 1);
+    DEC_TRY(cudaGetLastError());
+    g.start = counts;
+    g.items = ctx->grid_items.p;
+    ctx->launches += 6;  // count, scan (3), cursor copy, fill
+  }
+  int64_t blocks = (m + 127) / 128;
+  if (blocks > (int64_t)ctx->num_sms * 64) blocks = (int64_t)ctx->num_sms * 64;
+  hodge_tet_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 128, 0, s>>>(
+      ctx->xyz.p, ctx->tets.p, has_k ? ctx->kcond.p : nullptr,
+      m, ctx->piece.p, ctx->slot_cut.p, g);
+  DEC_TRY(cudaGetLastError());
+  int64_t eb = (ctx->ne + 255) / 256;
+  if (eb > (int64_t)ctx->num_sms * 32) eb = (int64_t)ctx->num_sms * 32;
+  edge_reduce_kernel<<<(unsigned)std::max<int64_t>(eb, 1), 256, 0, s>>>(
+      ctx->E.p, ctx->xyz.p, ctx->seg_start.p, ctx->seg_pay.p, ctx->piece.p,
+      ctx->slot_cut.p, ctx->ne, ctx->w.p, ctx->first_cut.p);
+  DEC_TRY(cudaGetLastError());
+  ctx->launches += 2;
+  return DEC_OK;
+}
+
+}  // namespace dec

@@ -1,0 +1,262 @@
+// dec_internal.cuh - context, device buffers and shared device helpers of
+// the GB300 DEC library.  Internal: not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/dec.h"
+
+namespace dec {
+
+// ---------------------------------------------------------------- buffers
+// A growable device allocation owned by the context; `ensure` reallocates
+// only when the requested size exceeds the capacity, so repeated calls on
+// meshes of the same size allocate nothing.
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t bytes = (n ? n : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) cap = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// ------------------------------------------------- device-side scalars
+// Scalars of one PCG instance kept in device memory so the iteration loop
+// never needs the host.  Reductions write them from the last block.
+struct CgScalars {
+  double rz;        // r . z
+  double pq;        // p . q
+  double rr;        // r . r
+  double alpha, beta;
+  double bnorm2;    // b . b
+  double tol2;      // (rtol * ||b||)^2
+  int done;         // 1 = converged or stopped: later kernels return at once
+  int iters;        // iterations taken
+  int breakdown;    // 1 = p.q <= 0 or not finite
+  int pad;
+};
+
+constexpr int kRedSlots = 4;           // values reduced by one kernel
+constexpr int kBlock = 256;            // threads per block, vector kernels
+
+}  // namespace dec
+
+// ----------------------------------------------------------------- context
+struct dec_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 152;
+  std::string err;
+  int stage = 0;  // 0 none, 1 mesh, 2 hodge, 3 laplacian, 4 solved
+
+  int64_t n = 0, m = 0, ne = 0, nnz = 0;
+  int n_sets = 1, n_scales = 1, B = 1;
+  int precond = DEC_PRECOND_JACOBI;
+  int reduce_grid = 0;  // blocks of the reducing vector kernels
+  int64_t launches = 0;  // kernels launched so far (graph nodes included)
+
+  // mesh
+  dec::DevBuf<double> xyz;
+  dec::DevBuf<int32_t> tets;
+  dec::DevBuf<uint8_t> tag;
+  dec::DevBuf<int32_t> E;          // [ne][2]
+  dec::DevBuf<int32_t> t2e;        // [m][6]
+  dec::DevBuf<uint32_t> seg_pay;   // [6m] tet*6+slot, grouped by edge
+  dec::DevBuf<int32_t> seg_start;  // [ne+1]
+  // sort / scan scratch
+  dec::DevBuf<uint64_t> key_a, key_b;
+  dec::DevBuf<uint32_t> val_a, val_b;
+  dec::DevBuf<uint32_t> hist, scan_tmp, flags;
+  dec::DevBuf<int> errflag;        // validation / limit flags
+  // Hodge star
+  dec::DevBuf<double> piece;       // [6m] k_T * signed dual area
+  dec::DevBuf<uint8_t> slot_cut;   // [6m] first crack state per slot
+  dec::DevBuf<double> w;           // [ne] uncracked *1
+  dec::DevBuf<uint8_t> first_cut;  // [ne]
+  dec::DevBuf<double> discs;       // [nd][7]
+  dec::DevBuf<double> scales;      // [n_scales]
+  dec::DevBuf<int32_t> grid_start, grid_items;
+  dec::DevBuf<double> kcond;       // [m]
+  // CSR of L
+  dec::DevBuf<int32_t> rowptr, col, eid, dpos, up_begin, lo_begin;
+  dec::DevBuf<int32_t> pos_up;     // [ne] CSR slot of (min, max)
+  dec::DevBuf<int32_t> lo_col, lo_eid;  // transposed edge list
+  // values of the current instance
+  dec::DevBuf<double> T0;          // [n_sets][n]
+  dec::DevBuf<double> val64;       // [B][nnz]
+  dec::DevBuf<float> val32;        // [B][nnz]
+  dec::DevBuf<double> b;           // [B][n]
+  dec::DevBuf<double> g64;         // [B][nnz] FSAI factor / Jacobi
+  dec::DevBuf<__nv_bfloat16> g16;  // [B][nnz]
+  dec::DevBuf<float> dinv32;       // [B][n]
+  dec::DevBuf<double> dinv64;      // [B][n]
+  // solver state
+  dec::DevBuf<double> x64, r64, z64, p64, q64, t64, u;  // u: [B][n] result
+  dec::DevBuf<float> x32, r32, z32, p32, q32, t32;
+  dec::DevBuf<double> partial;     // [kRedSlots][reduce_grid]
+  dec::DevBuf<unsigned> ticket;
+  dec::DevBuf<dec::CgScalars> cg;
+  dec::DevBuf<double> out3;        // k_eff outputs [B][3]
+  dec::DevBuf<uint8_t> flush;      // L2 eviction buffer (kernel timing only)
+  std::vector<int> iters_host;
+  std::vector<double> relres_host;
+
+  void release_all() {
+    xyz.release(); tets.release(); tag.release(); E.release(); t2e.release();
+    seg_pay.release(); seg_start.release(); key_a.release(); key_b.release();
+    val_a.release(); val_b.release(); hist.release(); scan_tmp.release();
+    flags.release(); errflag.release(); piece.release(); slot_cut.release();
+    w.release(); first_cut.release(); discs.release(); scales.release();
+    grid_start.release(); grid_items.release(); kcond.release(); rowptr.release();
+    col.release(); eid.release(); dpos.release(); up_begin.release();
+    lo_begin.release(); pos_up.release(); lo_col.release(); lo_eid.release();
+    T0.release(); val64.release(); val32.release(); b.release(); g64.release();
+    g16.release(); dinv32.release(); dinv64.release(); x64.release();
+    r64.release(); z64.release(); p64.release(); q64.release(); t64.release();
+    u.release(); x32.release(); r32.release(); z32.release(); p32.release();
+    q32.release(); t32.release(); partial.release(); ticket.release();
+    cg.release(); out3.release(); flush.release();
+  }
+
+  dec_status fail(dec_status s, const std::string& what) {
+    err = what;
+    return s;
+  }
+  dec_status cuda_fail(cudaError_t e, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return DEC_ERR_CUDA;
+  }
+};
+
+#define DEC_TRY(expr)                                       \
+  do {                                                      \
+    cudaError_t e__ = (expr);                               \
+    if (e__ != cudaSuccess) return ctx->cuda_fail(e__, #expr); \
+  } while (0)
+
+#define DEC_TRY_STATUS(expr)               \
+  do {                                     \
+    dec_status s__ = (expr);               \
+    if (s__ != DEC_OK) return s__;         \
+  } while (0)
+
+namespace dec {
+
+// ------------------------------------------------------ device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum `v` over the block into thread 0 (fixed order: deterministic).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    t = lane < NT / 32 ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// Deterministic grid reduction of NV doubles per thread.  Every block
+// stores its block sums in partial[slot * gridDim.x + block]; the last block
+// to arrive (integer ticket) sums the partials in block order and returns
+// true with the totals in `tot` (valid in all its threads).  Blocks that are
+// not last return false.
+template <int NT, int NV>
+__device__ __forceinline__ bool grid_reduce(const double (&v)[NV],
+                                            double (&tot)[NV],
+                                            double* partial,
+                                            unsigned* ticket) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+#pragma unroll
+  for (int s = 0; s < NV; ++s) {
+    double t = block_sum<NT>(v[s], sh);
+    if (threadIdx.x == 0) partial[s * gridDim.x + blockIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned k = atomicAdd(ticket, 1u);
+    last = (k == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int s = 0; s < NV; ++s) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += NT)
+      a += __ldcg(&partial[s * gridDim.x + i]);
+    double t = block_sum<NT>(a, sh);
+    __syncthreads();
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    tot[s] = sh[0];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+}  // namespace dec
+
+// ------------------------------------------------------ internal launches
+// (defined in the .cu files; all enqueue on ctx->stream)
+namespace dec {
+// scan / sort
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n,
+                               uint32_t* tmp, size_t tmp_cap, cudaStream_t s);
+size_t scan_tmp_size(int64_t n);
+dec_status radix_sort_pairs(dec_ctx* ctx, uint64_t* keys, uint32_t* vals,
+                            uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                            int key_bits, bool* result_in_alt);
+// mesh
+dec_status validate_mesh(dec_ctx* ctx);
+dec_status build_edges(dec_ctx* ctx);
+dec_status build_csr_structure(dec_ctx* ctx);
+// Hodge
+dec_status assemble_hodge(dec_ctx* ctx, int64_t n_discs, bool has_k);
+// system
+dec_status build_values(dec_ctx* ctx, int inst, bool want32);
+dec_status build_precond(dec_ctx* ctx, int inst, bool want16);
+// solve
+dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
+                          int mode, int* iters, double* relres);
+dec_status k_eff_instance(dec_ctx* ctx, int inst, double* out3);
+dec_status form_T(dec_ctx* ctx, int inst, double* T);
+dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
+                       double* avg_ms);
+}  // namespace dec

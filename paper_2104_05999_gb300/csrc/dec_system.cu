@@ -1,0 +1,237 @@
+// dec_system.cu - values of the node Laplacian L = d0^T *1 d0 with the
+// Dirichlet and zero-flux treatment of Sec. 2.3 (Eq. 11-13), the right-hand
+// sides, and the preconditioners: Jacobi and a factored sparse approximate
+// inverse (the ParaSails family of Sec. 2.3) on the pattern of lower(L).
+#include "dec_internal.cuh"
+
+#include <algorithm>
+
+namespace dec {
+
+// weight of edge e in crack state `state` (first_cut = first cut state)
+__device__ __forceinline__ double edge_weight(const double* w, const uint8_t* fc,
+                                              int32_t e, int state) {
+  return (int)fc[e] > state ? w[e] : 0.0;
+}
+
+// One thread per row.  Off-diagonal -w_ij (0 towards Dirichlet nodes, whose
+// values move to b), diagonal sum_j w_ij; Dirichlet rows and rows with all
+// weights zero become identity rows with b = 0.
+__global__ void laplacian_values_kernel(
+    int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const int32_t* __restrict__ eid, const int32_t* __restrict__ dpos,
+    const uint8_t* __restrict__ tag, const double* __restrict__ w,
+    const uint8_t* __restrict__ fc, int state, const double* __restrict__ T0,
+    double* __restrict__ val, float* __restrict__ val32, double* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k0 = rowptr[i], k1 = rowptr[i + 1], kd = dpos[i];
+    if (tag[i] == DEC_NODE_DIRICHLET) {
+      for (int32_t k = k0; k < k1; ++k) {
+        val[k] = k == kd ? 1.0 : 0.0;
+        if (val32) val32[k] = k == kd ? 1.0f : 0.0f;
+      }
+      b[i] = 0.0;
+      continue;
+    }
+    double diag = 0.0, bi = 0.0;
+    for (int32_t k = k0; k < k1; ++k) {
+      if (k == kd) continue;
+      const double we = edge_weight(w, fc, eid[k], state);
+      diag += we;
+      const int32_t j = col[k];
+      double v;
+      if (tag[j] == DEC_NODE_DIRICHLET) {
+        v = 0.0;
+        bi += we * T0[j];
+      } else {
+        v = we == 0.0 ? 0.0 : -we;
+      }
+      val[k] = v;
+      if (val32) val32[k] = (float)v;
+    }
+    if (diag == 0.0) {  // isolated by cracks: decoupled identity row
+      val[kd] = 1.0;
+      if (val32) val32[kd] = 1.0f;
+      b[i] = 0.0;
+    } else {
+      val[kd] = diag;
+      if (val32) val32[kd] = (float)diag;
+      b[i] = bi;
+    }
+  }
+}
+
+__global__ void jacobi_kernel(int64_t n, const int32_t* __restrict__ dpos,
+                              const double* __restrict__ val,
+                              double* __restrict__ dinv64,
+                              float* __restrict__ dinv32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double d = 1.0 / val[dpos[i]];
+    dinv64[i] = d;
+    if (dinv32) dinv32[i] = (float)d;
+  }
+}
+
+// ------------------------------------------------------------------ FSAI
+// One warp per row i.  P = columns of row i up to the diagonal (sorted,
+// ending with i), k = |P| <= kFsaiMax.  The warp gathers A = L[P, P] into
+// shared memory, factors A = C C^T (Cholesky, FP64) and back-substitutes
+// C^T g = e_k: then g = A^-1 e_k * C_kk and g_k = 1 / C_kk, so g equals
+// (A^-1 e_k) / sqrt((A^-1 e_k)_k), the FSAI row G[i, P].  A block whose
+// Cholesky meets a pivot <= kPivotRel * max(diag A) is singular: it is
+// factored again with kShiftRel * max(diag A) added to its diagonal.
+constexpr int kFsaiMax = 32;
+constexpr int kFsaiWarps = 4;
+constexpr double kPivotRel = 1e-12;
+constexpr double kShiftRel = 1e-12;
+
+__device__ void fsai_gather(int lane, int k, const int32_t* P,
+                            const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ col,
+                            const double* __restrict__ val, double (*A)[kFsaiMax + 1],
+                            double shift) {
+  for (int a = lane; a < k; a += 32) {
+    for (int q = 0; q < k; ++q) A[a][q] = 0.0;
+    const int32_t r = P[a];
+    int q = 0;
+    for (int32_t kk = rowptr[r]; kk < rowptr[r + 1] && q < k; ++kk) {
+      const int32_t c = col[kk];
+      while (q < k && P[q] < c) ++q;
+      if (q < k && P[q] == c) A[a][q] = val[kk];
+    }
+    A[a][a] += shift;
+  }
+}
+
+// returns false when a pivot is <= pivot_min (A is then partly overwritten)
+__device__ bool fsai_cholesky(int lane, int k, double (*A)[kFsaiMax + 1],
+                              double pivot_min) {
+  for (int c = 0; c < k; ++c) {
+    __syncwarp();
+    const double d = A[c][c];
+    if (!(d > pivot_min)) return false;
+    const double lc = sqrt(d);
+    __syncwarp();
+    if (lane > c && lane < k) A[lane][c] /= lc;
+    if (lane == c) A[c][c] = lc;
+    __syncwarp();
+    if (lane > c && lane < k) {
+      const double lrc = A[lane][c];
+      for (int q = c + 1; q <= lane; ++q) A[lane][q] -= lrc * A[q][c];
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
+__global__ void __launch_bounds__(32 * kFsaiWarps)
+fsai_setup_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                  const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
+                  const int32_t* __restrict__ dpos,
+                  const int32_t* __restrict__ pos_up,
+                  const double* __restrict__ val, double* __restrict__ g64,
+                  __nv_bfloat16* __restrict__ g16, int* errflag) {
+  __shared__ double Ash[kFsaiWarps][kFsaiMax][kFsaiMax + 1];
+  __shared__ int32_t Psh[kFsaiWarps][kFsaiMax];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double (*A)[kFsaiMax + 1] = Ash[wid];
+  int32_t* P = Psh[wid];
+  const int64_t warps = (int64_t)gridDim.x * kFsaiWarps;
+  for (int64_t i = blockIdx.x * (int64_t)kFsaiWarps + wid; i < n; i += warps) {
+    const int32_t k0 = rowptr[i], kd = dpos[i];
+    const int k = kd - k0 + 1;
+    if (k > kFsaiMax) {
+      if (lane == 0) atomicOr(errflag, 8);
+      continue;
+    }
+    __syncwarp();
+    if (lane < k) P[lane] = col[k0 + lane];
+    __syncwarp();
+    fsai_gather(lane, k, P, rowptr, col, val, A, 0.0);
+    __syncwarp();
+    double dmax = lane < k ? A[lane][lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if (!fsai_cholesky(lane, k, A, kPivotRel * dmax)) {
+      __syncwarp();
+      fsai_gather(lane, k, P, rowptr, col, val, A, kShiftRel * dmax);
+      __syncwarp();
+      fsai_cholesky(lane, k, A, 0.0);
+    }
+    // back substitution C^T g = e_k; lane a holds rhs_a, then g_a
+    double rhs = (lane == k - 1) ? 1.0 : 0.0;
+    double g = 0.0;
+    for (int j = k - 1; j >= 0; --j) {
+      double gj = 0.0;
+      if (lane == j) gj = rhs / A[j][j];
+      gj = __shfl_sync(0xffffffffu, gj, j);
+      if (lane == j) g = gj;
+      if (lane < j) rhs -= A[j][lane] * gj;
+    }
+    if (lane < k) {
+      const int32_t pos = k0 + lane;
+      g64[pos] = g;
+      if (g16) g16[pos] = __float2bfloat16_rn((float)g);
+      if (lane < k - 1) {  // transpose slot: entry (P[lane], i) in row P[lane]
+        const int32_t tp = pos_up[eid[pos]];
+        g64[tp] = g;
+        if (g16) g16[tp] = __float2bfloat16_rn((float)g);
+      }
+    }
+  }
+}
+
+static unsigned grid_rows(const dec_ctx* ctx, int64_t work, int per_block) {
+  int64_t g = (work + per_block - 1) / per_block;
+  int64_t cap = (int64_t)ctx->num_sms * 32;
+  return (unsigned)std::max<int64_t>(1, std::min(g, cap));
+}
+
+dec_status build_values(dec_ctx* ctx, int inst, bool want32) {
+  const int64_t n = ctx->n, nnz = ctx->nnz;
+  const int vs = ctx->n_scales > 1 ? inst : 0;      // value set
+  const int ts = ctx->n_sets > 1 ? inst : 0;        // Dirichlet set
+  double* val = ctx->val64.p + (int64_t)vs * nnz;
+  float* v32 = want32 ? ctx->val32.p + (int64_t)vs * nnz : nullptr;
+  laplacian_values_kernel<<<grid_rows(ctx, n, 256), 256, 0, ctx->stream>>>(
+      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->w.p,
+      ctx->first_cut.p, ctx->n_scales > 1 ? inst : 0, ctx->T0.p + (int64_t)ts * n,
+      val, v32, ctx->b.p + (int64_t)inst * n);
+  DEC_TRY(cudaGetLastError());
+  ctx->launches += 1;
+  return DEC_OK;
+}
+
+dec_status build_precond(dec_ctx* ctx, int inst, bool want16) {
+  const int64_t n = ctx->n, nnz = ctx->nnz;
+  const int vs = ctx->n_scales > 1 ? inst : 0;
+  const double* val = ctx->val64.p + (int64_t)vs * nnz;
+  cudaStream_t s = ctx->stream;
+  if (ctx->precond == DEC_PRECOND_JACOBI) {
+    jacobi_kernel<<<grid_rows(ctx, n, 256), 256, 0, s>>>(
+        n, ctx->dpos.p, val, ctx->dinv64.p + (int64_t)vs * n,
+        ctx->dinv32.p ? ctx->dinv32.p + (int64_t)vs * n : nullptr);
+    DEC_TRY(cudaGetLastError());
+    ctx->launches += 1;
+    return DEC_OK;
+  }
+  DEC_TRY(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
+  fsai_setup_kernel<<<grid_rows(ctx, n, kFsaiWarps), 32 * kFsaiWarps, 0, s>>>(
+      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->pos_up.p, val,
+      ctx->g64.p + (int64_t)vs * nnz,
+      want16 ? ctx->g16.p + (int64_t)vs * nnz : nullptr, ctx->errflag.p);
+  DEC_TRY(cudaGetLastError());
+  ctx->launches += 1;
+  int flag = 0;
+  DEC_TRY(cudaMemcpyAsync(&flag, ctx->errflag.p, sizeof(int),
+                          cudaMemcpyDeviceToHost, s));
+  DEC_TRY(cudaStreamSynchronize(s));
+  if (flag & 8)
+    return ctx->fail(DEC_ERR_LIMIT, "an FSAI row has more than 32 lower-pattern entries");
+  return DEC_OK;
+}
+
+}  // namespace dec
