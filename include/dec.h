@@ -71,9 +71,12 @@ enum { DEC_PRECOND_JACOBI = 0, DEC_PRECOND_FSAI = 1 };
 /* solve modes (dec_solve) */
 enum {
   DEC_MODE_FP64 = 0,   /* PCG in FP64 (matrix, preconditioner, vectors)       */
-  DEC_MODE_MIXED = 1   /* FP32 PCG with a BF16 FSAI factor (FP32 Jacobi)
-                          inside FP64 defect correction: r = b - L x in FP64,
-                          inner solve of L e = r in FP32, x += e             */
+  DEC_MODE_MIXED = 1   /* PCG with FP32 vectors and L and a BF16 FSAI factor
+                          (FP32 Jacobi) inside FP64 defect correction: the
+                          FP32 update is added to an FP64 solution x and the
+                          FP32 residual replaced by r = b - L x in FP64 each
+                          time it has dropped by 1e-2, keeping the search
+                          direction; convergence is decided in FP64        */
 };
 
 /* Local edge slots of a tet: slot s joins local vertices LOCAL[s] =

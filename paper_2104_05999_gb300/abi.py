@@ -233,3 +233,4 @@ class Context:
         self._check(self.lib.dec_time_kernel(self.h, int(kernel), int(reps),
                                              int(flush_bytes), C.byref(ms)))
         return ms.value
+

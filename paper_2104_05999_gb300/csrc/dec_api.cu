@@ -132,6 +132,13 @@ dec_status dec_mesh_upload(dec_ctx* ctx, const double* xyz, int64_t n_nodes,
   DEC_TRY_STATUS(dec::validate_mesh(ctx));
   DEC_TRY_STATUS(dec::build_edges(ctx));
   DEC_TRY_STATUS(dec::build_csr_structure(ctx));
+  DEC_TRY_STATUS(dec::build_sell_layouts(ctx));
+  ctx->grid_vec = (int)std::max<int64_t>(
+      1, std::min<int64_t>((n_nodes + dec::kBlock - 1) / dec::kBlock, (int64_t)ctx->num_sms * 2));
+  ctx->grid_sell = (int)std::max<int64_t>(
+      1, std::min<int64_t>((ctx->sellL.nslices + 7) / 8, (int64_t)ctx->num_sms * 4));
+  ctx->reduce_grid = std::max(ctx->grid_vec, ctx->grid_sell);
+  DEC_TRY(ctx->partial.ensure((size_t)dec::kRedSlots * ctx->reduce_grid));
   DEC_TRY(cudaStreamSynchronize(s));
   ctx->stage = 1;
   return DEC_OK;
@@ -154,12 +161,8 @@ dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k, const double* discs
   // conductivity: finite and > 0
   const bool has_k = k != nullptr;
   if (has_k) {
-    std::vector<double> hk;
-    DEC_TRY(host_copy(hk, k, ctx->m, s));
-    for (double v : hk)
-      if (!(v > 0.0) || !std::isfinite(v))
-        return ctx->fail(DEC_ERR_ARG, "hodge_assemble: conductivity must be finite and > 0");
-    DEC_TRY(upload(ctx->kcond, hk.data(), ctx->m, s));
+    DEC_TRY(upload(ctx->kcond, k, ctx->m, s));
+    DEC_TRY_STATUS(dec::validate_k(ctx));
   }
   std::vector<double> hs;
   if (scales) {
@@ -211,18 +214,21 @@ dec_status dec_laplacian_build(dec_ctx* ctx, const double* T0, int32_t n_sets,
   const int V = ctx->n_scales;  // value sets
   DEC_TRY(upload(ctx->T0, T0, (int64_t)n_sets * n, s));
   DEC_TRY(ctx->val64.ensure((size_t)V * nnz));
-  DEC_TRY(ctx->val32.ensure((size_t)V * nnz));
+  DEC_TRY(ctx->sL64.ensure((size_t)V * ctx->sellL.total));
+  DEC_TRY(ctx->sL32.ensure((size_t)V * ctx->sellL.total));
   DEC_TRY(ctx->b.ensure((size_t)ctx->B * n));
   if (precond == DEC_PRECOND_FSAI) {
     DEC_TRY(ctx->g64.ensure((size_t)V * nnz));
-    DEC_TRY(ctx->g16.ensure((size_t)V * nnz));
+    DEC_TRY(ctx->sGlo64.ensure((size_t)V * ctx->sellLo.total));
+    DEC_TRY(ctx->sGup64.ensure((size_t)V * ctx->sellUp.total));
+    DEC_TRY(ctx->sGlo16.ensure((size_t)V * ctx->sellLo.total));
+    DEC_TRY(ctx->sGup16.ensure((size_t)V * ctx->sellUp.total));
   } else {
     DEC_TRY(ctx->dinv64.ensure((size_t)V * n));
     DEC_TRY(ctx->dinv32.ensure((size_t)V * n));
   }
-  for (int inst = 0; inst < ctx->B; ++inst)
-    DEC_TRY_STATUS(dec::build_values(ctx, inst, true));
-  for (int vs = 0; vs < V; ++vs) DEC_TRY_STATUS(dec::build_precond(ctx, vs, true));
+  for (int inst = 0; inst < ctx->B; ++inst) DEC_TRY_STATUS(dec::build_values(ctx, inst));
+  for (int vs = 0; vs < V; ++vs) DEC_TRY_STATUS(dec::build_precond(ctx, vs));
   DEC_TRY(cudaStreamSynchronize(s));
   ctx->stage = 3;
   return DEC_OK;

@@ -3,17 +3,20 @@
 // conductivity of each tet scaling its share (Sec. 2.1) and penny cracks
 // making cut dual faces insulating (Sec. 2.5).
 //
-// One thread per tet computes, in FP64, its circumcentre, the circumcentres
-// and inward unit normals of its 4 faces, and for each of its 6 edges the
-// signed area of the dual-face piece inside the tet:
-//   piece = k_T * sum over the 2 faces F of the tet that contain e of
-//           (1/2) * h1(F) * h2(F),
-//   h1 = signed distance, inside F, from the edge midpoint to c_F
-//        (+ towards F's third vertex),
-//   h2 = signed distance from c_T to the plane of F (+ towards the tet's
-//        fourth vertex).
-// Each half (m_e, c_F, c_T) is a right triangle in the bisector plane of e;
-// the crack test runs on exactly these triangles.  A second pass sums the
+// One thread per tet computes, in FP64, for each of its 6 edges the signed
+// area of the dual-face piece inside the tet divided by the edge length.
+// The piece of edge e = (a, b) splits into two right triangles (m_e, c_F,
+// c_T), one per face F = {a, b, c} of the tet containing e: legs h1 = signed
+// distance from the midpoint m_e to c_F inside F (+ towards c) and h2 =
+// signed distance from c_T to the plane of F (+ towards the fourth vertex).
+// With h1 = |e|/2 cot(angle at c), cot = (x_a-x_c).(x_b-x_c) / |N_F| and
+// h2 = (c_T - x_a).N_F / |N_F| (N_F the inward face normal, |N_F| = twice
+// the face area), each half contributes
+//   (1/2) h1 h2 / |e| = (1/4) (x_a-x_c).(x_b-x_c) (c_T - x_a).N_F / |N_F|^2,
+// so the kernel needs one division per face and none per edge (FP64
+// division and square root are expensive on GB300).  The crack test runs on
+// the sub-triangles themselves, with face circumcentres computed only when
+// discs are present.  A second pass sums the
 // pieces of every edge in a fixed order (sorted tet*6+slot), so *1 is
 // deterministic without atomics.
 #include "dec_internal.cuh"
@@ -117,47 +120,50 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
       X[i] = mk(xyz[3 * (int64_t)vid[i]], xyz[3 * (int64_t)vid[i] + 1],
                 xyz[3 * (int64_t)vid[i] + 2]);
     const double kT = kcond ? kcond[t] : 1.0;
-    // tet circumcentre: x0 + (|a|^2 (b x c) + |b|^2 (c x a) + |c|^2 (a x b)) / (2 a.(b x c))
-    V3 a = X[1] - X[0], b = X[2] - X[0], c = X[3] - X[0];
-    V3 bxc = cross(b, c), cxa = cross(c, a), axb = cross(a, b);
-    double det6 = dot(a, bxc);
-    V3 cT = X[0] + (0.5 / det6) * (dot(a, a) * bxc + dot(b, b) * cxa + dot(c, c) * axb);
-    // face opposite vertex v: circumcentre and unit normal pointing to v
-    V3 cF[4], nin[4];
+    // all vectors relative to X[0]
+    V3 R[4];
+    R[0] = mk(0.0, 0.0, 0.0);
+#pragma unroll
+    for (int i = 1; i < 4; ++i) R[i] = X[i] - X[0];
+    // tet circumcentre: (|a|^2 (b x c) + |b|^2 (c x a) + |c|^2 (a x b)) / (2 a.(b x c))
+    const V3 bxc = cross(R[2], R[3]), cxa = cross(R[3], R[1]), axb = cross(R[1], R[2]);
+    const double det6 = dot(R[1], bxc);
+    const V3 cT = (0.5 / det6) * (dot(R[1], R[1]) * bxc + dot(R[2], R[2]) * cxa +
+                                  dot(R[3], R[3]) * axb);
+    // H[v]: signed distance from c_T to the face opposite v (+ towards v),
+    // divided by twice the face area: ((c_T - x).N) / |N|^2, N = inward normal
+    double H[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int i0 = (v + 1) & 3, i1 = (v + 2) & 3, i2 = (v + 3) & 3;
-      cF[v] = tri_circumcentre(X[i0], X[i1], X[i2]);
-      V3 nn = cross(X[i1] - X[i0], X[i2] - X[i0]);
-      double s = dot(nn, X[v] - X[i0]) > 0.0 ? 1.0 : -1.0;
-      nin[v] = (s / sqrt(dot(nn, nn))) * nn;
+      const V3 nn = cross(R[i1] - R[i0], R[i2] - R[i0]);
+      const double side = dot(nn, R[v] - R[i0]);
+      const double h = dot(cT - R[i0], nn) / dot(nn, nn);
+      H[v] = side > 0.0 ? h : -h;
     }
+    // Half of the dual face of edge (a,b) inside face F = {a,b,c}: right
+    // triangle (m_e, c_F, c_T) with legs |e|/2 * cot(angle at c) and the
+    // distance from c_T to F.  With cot = (x_a-x_c).(x_b-x_c) / |N_F| its
+    // area over |e| is (1/4) (x_a-x_c).(x_b-x_c) * H_F.
     uint8_t first[6];
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
       const int ea = kEdgeA[s], eb = kEdgeB[s], ec = kEdgeC[s], ed = kEdgeD[s];
-      V3 me = 0.5 * (X[ea] + X[eb]);
-      V3 e = X[eb] - X[ea];
-      double ee = dot(e, e);
-      double area = 0.0;
-      // face {a,b,c} is opposite d (third vertex c); face {a,b,d} opposite c
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int third = h == 0 ? ec : ed;
-        const int opp = h == 0 ? ed : ec;
-        V3 w = X[third] - me;
-        V3 tv = w - (dot(w, e) / ee) * e;          // in F, normal to e
-        double h1 = dot(cF[opp] - me, tv) / sqrt(dot(tv, tv));
-        double h2 = dot(cT - cF[opp], nin[opp]);
-        area += 0.5 * h1 * h2;
-      }
-      piece[t * 6 + s] = kT * area;
+      const double cot_c = dot(R[ea] - R[ec], R[eb] - R[ec]);   // face opposite d
+      const double cot_d = dot(R[ea] - R[ed], R[eb] - R[ed]);   // face opposite c
+      piece[t * 6 + s] = kT * 0.25 * (cot_c * H[ed] + cot_d * H[ec]);
       first[s] = (uint8_t)grid.n_states;
     }
     if (grid.nd > 0) {
+      // absolute points of the dual sub-triangles
+      const V3 cTa = X[0] + cT;
+      V3 cF[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        cF[v] = tri_circumcentre(X[(v + 1) & 3], X[(v + 2) & 3], X[(v + 3) & 3]);
       // bounding box of the 12 dual sub-triangles of the tet
       double lo[3], hi[3];
-      lo[0] = hi[0] = cT.x; lo[1] = hi[1] = cT.y; lo[2] = hi[2] = cT.z;
+      lo[0] = hi[0] = cTa.x; lo[1] = hi[1] = cTa.y; lo[2] = hi[2] = cTa.z;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         lo[0] = fmin(lo[0], fmin(cF[v].x, X[v].x)); hi[0] = fmax(hi[0], fmax(cF[v].x, X[v].x));
@@ -186,7 +192,7 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int opp = h == 0 ? kEdgeD[s] : kEdgeC[s];
-            double rho = crack_rho(me, cF[opp], cT, dc, dn);
+            double rho = crack_rho(me, cF[opp], cTa, dc, dn);
             for (int st = 0; st < (int)first[s]; ++st)
               if (rho <= grid.scales[st] * r) {
                 first[s] = (uint8_t)st;
@@ -217,11 +223,9 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
   }
 }
 
-// *1[e] = (sum of the pieces of e, in increasing tet*6+slot) / |e|;
-// first_cut[e] = min over those slots.
-__global__ void edge_reduce_kernel(const int32_t* __restrict__ E,
-                                   const double* __restrict__ xyz,
-                                   const int32_t* __restrict__ seg_start,
+// *1[e] = sum of the pieces of e (already divided by |e|), in increasing
+// tet*6+slot order; first_cut[e] = min over those slots.
+__global__ void edge_reduce_kernel(const int32_t* __restrict__ seg_start,
                                    const uint32_t* __restrict__ seg_pay,
                                    const double* __restrict__ piece,
                                    const uint8_t* __restrict__ slot_cut,
@@ -236,11 +240,7 @@ __global__ void edge_reduce_kernel(const int32_t* __restrict__ E,
       sum += piece[p];
       fc = min(fc, (unsigned)slot_cut[p]);
     }
-    int2 ij = reinterpret_cast<const int2*>(E)[e];
-    double dx = xyz[3 * (int64_t)ij.y] - xyz[3 * (int64_t)ij.x];
-    double dy = xyz[3 * (int64_t)ij.y + 1] - xyz[3 * (int64_t)ij.x + 1];
-    double dz = xyz[3 * (int64_t)ij.y + 2] - xyz[3 * (int64_t)ij.x + 2];
-    w[e] = sum / sqrt(dx * dx + dy * dy + dz * dz);
+    w[e] = sum;
     first_cut[e] = (uint8_t)fc;
   }
 }
@@ -273,6 +273,30 @@ __global__ void copy_i32_kernel(const int32_t* a, int32_t* b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     b[i] = a[i];
+}
+
+__global__ void validate_k_kernel(const double* __restrict__ k, int64_t m, int* errflag) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double v = k[t];
+    if (!(v > 0.0) || !isfinite(v)) atomicOr(errflag, 16);
+  }
+}
+
+// conductivity must be finite and > 0 (checked on the device)
+dec_status validate_k(dec_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  DEC_TRY(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
+  const unsigned g = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((ctx->m + 255) / 256, (int64_t)ctx->num_sms * 16));
+  validate_k_kernel<<<g, 256, 0, s>>>(ctx->kcond.p, ctx->m, ctx->errflag.p);
+  DEC_TRY(cudaGetLastError());
+  ctx->launches += 1;
+  int flag = 0;
+  DEC_TRY(cudaMemcpyAsync(&flag, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DEC_TRY(cudaStreamSynchronize(s));
+  if (flag & 16) return ctx->fail(DEC_ERR_ARG, "hodge_assemble: conductivity must be finite and > 0");
+  return DEC_OK;
 }
 
 dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k) {
@@ -346,8 +370,8 @@ dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k) {
   int64_t eb = (ctx->ne + 255) / 256;
   if (eb > (int64_t)ctx->num_sms * 32) eb = (int64_t)ctx->num_sms * 32;
   edge_reduce_kernel<<<(unsigned)std::max<int64_t>(eb, 1), 256, 0, s>>>(
-      ctx->E.p, ctx->xyz.p, ctx->seg_start.p, ctx->seg_pay.p, ctx->piece.p,
-      ctx->slot_cut.p, ctx->ne, ctx->w.p, ctx->first_cut.p);
+      ctx->seg_start.p, ctx->seg_pay.p, ctx->piece.p, ctx->slot_cut.p, ctx->ne,
+      ctx->w.p, ctx->first_cut.p);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 2;
   return DEC_OK;

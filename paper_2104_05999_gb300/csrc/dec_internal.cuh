@@ -54,6 +54,18 @@ struct CgScalars {
   int pad;
 };
 
+// Sliced-ELLPACK layout of one matrix sharing L's CSR structure (slices of
+// 32 rows, one lane per row, rows sorted by length inside 512-row windows).
+struct SellLayout {
+  DevBuf<int32_t> perm;   // [nslices*32] row of each (slice, lane), -1 = none
+  DevBuf<int32_t> len;    // [nslices*32] row length in slot order
+  DevBuf<int32_t> sptr;   // [nslices+1] first entry of each slice
+  DevBuf<int32_t> col;    // [total] column of entry j of lane l: sptr[s]+32j+l
+  DevBuf<int32_t> pos;    // [nnz] CSR slot -> SELL slot, -1 if absent
+  int64_t nslices = 0, total = 0;
+  void release() { perm.release(); len.release(); sptr.release(); col.release(); pos.release(); }
+};
+
 constexpr int kRedSlots = 4;           // values reduced by one kernel
 constexpr int kBlock = 256;            // threads per block, vector kernels
 
@@ -71,7 +83,9 @@ struct dec_ctx {
   int64_t n = 0, m = 0, ne = 0, nnz = 0;
   int n_sets = 1, n_scales = 1, B = 1;
   int precond = DEC_PRECOND_JACOBI;
-  int reduce_grid = 0;  // blocks of the reducing vector kernels
+  int reduce_grid = 0;  // capacity (blocks) of the reduction partials
+  int grid_vec = 0;     // blocks of the element-wise vector kernels
+  int grid_sell = 0;    // blocks of the SELL kernels (one slice per warp)
   int64_t launches = 0;  // kernels launched so far (graph nodes included)
 
   // mesh
@@ -102,11 +116,9 @@ struct dec_ctx {
   dec::DevBuf<int32_t> lo_col, lo_eid;  // transposed edge list
   // values of the current instance
   dec::DevBuf<double> T0;          // [n_sets][n]
-  dec::DevBuf<double> val64;       // [B][nnz]
-  dec::DevBuf<float> val32;        // [B][nnz]
+  dec::DevBuf<double> val64;       // [V][nnz] CSR values per value set
   dec::DevBuf<double> b;           // [B][n]
-  dec::DevBuf<double> g64;         // [B][nnz] FSAI factor / Jacobi
-  dec::DevBuf<__nv_bfloat16> g16;  // [B][nnz]
+  dec::DevBuf<double> g64;         // [V][nnz] FSAI factor (CSR layout)
   dec::DevBuf<float> dinv32;       // [B][n]
   dec::DevBuf<double> dinv64;      // [B][n]
   // solver state
@@ -117,6 +129,12 @@ struct dec_ctx {
   dec::DevBuf<dec::CgScalars> cg;
   dec::DevBuf<double> out3;        // k_eff outputs [B][3]
   dec::DevBuf<uint8_t> flush;      // L2 eviction buffer (kernel timing only)
+  // solver layouts (SELL-32-512) and their value arrays, per value set
+  dec::SellLayout sellL, sellLo, sellUp;
+  dec::DevBuf<double> sL64, sGlo64, sGup64;
+  dec::DevBuf<float> sL32;
+  dec::DevBuf<__nv_bfloat16> sGlo16, sGup16;
+  dec::DevBuf<int32_t> big_rows;   // FSAI rows for the warp-per-row kernel
   std::vector<int> iters_host;
   std::vector<double> relres_host;
 
@@ -129,12 +147,15 @@ struct dec_ctx {
     grid_start.release(); grid_items.release(); kcond.release(); rowptr.release();
     col.release(); eid.release(); dpos.release(); up_begin.release();
     lo_begin.release(); pos_up.release(); lo_col.release(); lo_eid.release();
-    T0.release(); val64.release(); val32.release(); b.release(); g64.release();
-    g16.release(); dinv32.release(); dinv64.release(); x64.release();
+    T0.release(); val64.release(); b.release(); g64.release();
+    dinv32.release(); dinv64.release(); x64.release();
     r64.release(); z64.release(); p64.release(); q64.release(); t64.release();
     u.release(); x32.release(); r32.release(); z32.release(); p32.release();
     q32.release(); t32.release(); partial.release(); ticket.release();
     cg.release(); out3.release(); flush.release();
+    sellL.release(); sellLo.release(); sellUp.release(); sL64.release();
+    sGlo64.release(); sGup64.release(); sL32.release(); sGlo16.release();
+    sGup16.release(); big_rows.release();
   }
 
   dec_status fail(dec_status s, const std::string& what) {
@@ -247,11 +268,15 @@ dec_status radix_sort_pairs(dec_ctx* ctx, uint64_t* keys, uint32_t* vals,
 dec_status validate_mesh(dec_ctx* ctx);
 dec_status build_edges(dec_ctx* ctx);
 dec_status build_csr_structure(dec_ctx* ctx);
+dec_status build_sell_layouts(dec_ctx* ctx);
+template <typename T>
+dec_status scatter_values(dec_ctx* ctx, const SellLayout& L, const double* csr_val, T* out);
 // Hodge
 dec_status assemble_hodge(dec_ctx* ctx, int64_t n_discs, bool has_k);
+dec_status validate_k(dec_ctx* ctx);
 // system
-dec_status build_values(dec_ctx* ctx, int inst, bool want32);
-dec_status build_precond(dec_ctx* ctx, int inst, bool want16);
+dec_status build_values(dec_ctx* ctx, int inst);
+dec_status build_precond(dec_ctx* ctx, int vs);
 // solve
 dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
                           int mode, int* iters, double* relres);

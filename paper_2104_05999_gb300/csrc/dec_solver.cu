@@ -7,12 +7,14 @@
 // the producing kernel (block partials, the last block finishes in a fixed
 // order), so results are deterministic and the host only polls a `done`
 // flag once per chunk of iterations.  A chunk is captured once into a CUDA
-// graph and replayed.
+// graph and replayed.  Matrix products use the SELL-32-512 layout built in
+// dec_sell.cu: one warp per slice of 32 rows, one lane per row.
 //
 //   FP64 mode : x, r, z, p, q in FP64; L and the preconditioner in FP64.
-//   mixed mode: FP64 defect correction r = b - L x around an inner PCG whose
-//               vectors and L are FP32 and whose FSAI factor is BF16 (or an
-//               FP32 Jacobi); x += e after every inner solve.
+//   mixed mode: PCG with FP32 vectors and L and a BF16 FSAI factor (or an
+//               FP32 Jacobi), whose residual is replaced by the FP64 residual
+//               b - L x of an FP64 solution x every time it has dropped by
+//               1e-2 (defect correction that keeps the search direction).
 #include "dec_internal.cuh"
 
 #include <algorithm>
@@ -22,38 +24,63 @@ namespace dec {
 
 __device__ __forceinline__ double to_d(double v) { return v; }
 __device__ __forceinline__ double to_d(float v) { return (double)v; }
-__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename T> struct Acc;           // row accumulation type
-template <> struct Acc<double> { using type = double; };
-template <> struct Acc<float> { using type = float; };
+__device__ __forceinline__ double fma_(double a, double x, double acc) { return fma(a, x, acc); }
+__device__ __forceinline__ float fma_(float a, float x, float acc) { return fmaf(a, x, acc); }
+__device__ __forceinline__ float fma_(__nv_bfloat16 a, float x, float acc) {
+  return fmaf(__bfloat162float(a), x, acc);
+}
 
-template <typename VT, typename MT>
-__device__ __forceinline__ VT mul_acc(VT acc, MT a, VT x);
-template <> __device__ __forceinline__ double mul_acc(double acc, double a, double x) { return fma(a, x, acc); }
-template <> __device__ __forceinline__ float mul_acc(float acc, float a, float x) { return fmaf(a, x, acc); }
-template <> __device__ __forceinline__ float mul_acc(float acc, __nv_bfloat16 a, float x) { return fmaf(__bfloat162float(a), x, acc); }
-template <> __device__ __forceinline__ double mul_acc(double acc, __nv_bfloat16 a, double x) { return fma((double)__bfloat162float(a), x, acc); }
+// Matrix in SELL form, as kernel arguments.
+template <typename T>
+struct SellArg {
+  const int32_t* perm;
+  const int32_t* sptr;
+  const int32_t* col;
+  const T* val;
+  int64_t nslices;
+};
 
-// Sum over entries k in [k0, k1) of a[k] * x[col[k]] by a group of TPR lanes;
-// the total is returned in every lane of the group.
-template <int TPR, typename MT, typename VT>
-__device__ __forceinline__ VT row_sum(int lir, int32_t k0, int32_t k1,
-                                      const int32_t* __restrict__ col,
-                                      const MT* __restrict__ a,
-                                      const VT* __restrict__ x) {
-  VT s = VT(0);
-  for (int32_t k = k0 + lir; k < k1; k += TPR) s = mul_acc(s, a[k], __ldg(x + col[k]));
+template <typename T>
+static SellArg<T> sell_arg(const SellLayout& L, const T* val) {
+  return SellArg<T>{L.perm.p, L.sptr.p, L.col.p, val, L.nslices};
+}
+
+// Row sum of the lane's row in slice s: sum_j val * x[col].  Entries are
+// taken 8 at a time: 8 column and 8 value loads, then 8 independent gathers,
+// then the FMAs, so each warp keeps many loads in flight (the width w is
+// uniform across the warp, so the guards never diverge).
+template <typename MT, typename VT>
+__device__ __forceinline__ VT sell_row(const SellArg<MT>& A, int64_t s, int lane,
+                                       const VT* __restrict__ x) {
+  constexpr int U = 8;
+  const int32_t base = __ldg(A.sptr + s);
+  const int32_t w = (__ldg(A.sptr + s + 1) - base) >> 5;
+  const int32_t* __restrict__ cp = A.col + base + lane;
+  const MT* __restrict__ vp = A.val + base + lane;
+  VT acc = VT(0);
+  for (int32_t j = 0; j < w; j += U) {
+    int32_t c[U];
+    MT a[U];
+    VT xv[U];
 #pragma unroll
-  for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
-  return s;
+    for (int u = 0; u < U; ++u) {
+      const bool ok = j + u < w;
+      c[u] = ok ? __ldg(cp + 32 * (j + u)) : 0;
+      a[u] = ok ? vp[32 * (j + u)] : MT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = j + u < w ? __ldg(x + c[u]) : VT(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j + u < w) acc = fma_(a[u], xv[u], acc);   // uniform: no idle FMAs
+  }
+  return acc;
 }
 
 // ------------------------------------------------------------ kernels
-// Launch shape of the vector kernels: fixed grid (reduce_grid blocks of
-// kBlock threads), grid-stride over rows.
+// Element-wise kernels run grid_vec blocks (grid-stride over rows); SELL
+// kernels run grid_sell blocks, one slice per warp.
 
 template <typename BT, typename VT>
 __global__ void __launch_bounds__(kBlock)
@@ -83,25 +110,21 @@ cg_init_kernel(int64_t n, const BT* __restrict__ b, VT* __restrict__ x,
 }
 
 // q = A p and alpha = (r.z) / (p.q)
-template <int TPR, typename MT, typename VT>
+template <typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock)
-spmv_pq_kernel(int64_t n, const int32_t* __restrict__ rowptr,
-               const int32_t* __restrict__ col, const MT* __restrict__ val,
-               const VT* __restrict__ p, VT* __restrict__ q, CgScalars* cg,
-               double* partial, unsigned* ticket) {
+spmv_pq_kernel(SellArg<MT> A, const VT* __restrict__ p, VT* __restrict__ q,
+               CgScalars* cg, double* partial, unsigned* ticket) {
   if (*(volatile int*)&cg->done) return;
-  const int lir = threadIdx.x % TPR;
-  const int64_t groups = (int64_t)gridDim.x * (kBlock / TPR);
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (kBlock / 32);
   double pq = 0.0;
-  // all lanes of a group run the same number of loop trips (n rounded up)
-  for (int64_t i = blockIdx.x * (int64_t)(kBlock / TPR) + threadIdx.x / TPR;
-       i - (int64_t)(threadIdx.x / TPR) < n; i += groups) {
-    const bool ok = i < n;
-    const int32_t k0 = ok ? rowptr[i] : 0, k1 = ok ? rowptr[i + 1] : 0;
-    VT s = row_sum<TPR>(lir, k0, k1, col, val, p);
-    if (ok && lir == 0) {
-      q[i] = s;
-      pq += to_d(p[i]) * to_d(s);
+  for (int64_t s = blockIdx.x * (int64_t)(kBlock / 32) + (threadIdx.x >> 5);
+       s < A.nslices; s += warps) {
+    const int32_t r = __ldg(A.perm + 32 * s + lane);
+    const VT acc = sell_row(A, s, lane, p);
+    if (r >= 0) {
+      q[r] = acc;
+      pq += to_d(p[r]) * to_d(acc);
     }
   }
   double v[1] = {pq}, t[1];
@@ -118,7 +141,11 @@ spmv_pq_kernel(int64_t n, const int32_t* __restrict__ rowptr,
   }
 }
 
-// x += alpha p, r -= alpha q, r.r; with Jacobi also z = dinv r and r.z
+// x += alpha p, r -= alpha q, r.r; with Jacobi also z = dinv r and r.z.
+// Element-wise kernels run few blocks with 4 elements per thread in flight:
+// GB300's FP64 pipe is narrow, so the per-warp cost of the FP64 reductions
+// has to be spread over several elements per thread.  Per-thread sums are
+// kept in the vector type and widened to FP64 before the warp reduction.
 template <typename VT, typename DT, bool JACOBI>
 __global__ void __launch_bounds__(kBlock)
 update_kernel(int64_t n, VT* __restrict__ x, VT* __restrict__ r,
@@ -127,72 +154,84 @@ update_kernel(int64_t n, VT* __restrict__ x, VT* __restrict__ r,
               CgScalars* cg, double* partial, unsigned* ticket) {
   if (*(volatile int*)&cg->done) return;
   const VT alpha = (VT)cg->alpha;
-  double rr = 0.0, rz = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    VT xi = x[i] + alpha * p[i];
-    VT ri = r[i] - alpha * q[i];
-    x[i] = xi;
-    r[i] = ri;
-    rr += to_d(ri) * to_d(ri);
+  VT rr = VT(0), rz = VT(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  auto one = [&](int64_t k, VT pk, VT qk, VT xk, VT rk) {
+    const VT ri = fma_(-alpha, qk, rk);
+    x[k] = fma_(alpha, pk, xk);
+    r[k] = ri;
+    rr = fma_(ri, ri, rr);
     if (JACOBI) {
-      VT zi = (VT)dinv[i] * ri;
-      z[i] = zi;
-      rz += to_d(ri) * to_d(zi);
+      const VT zi = (VT)dinv[k] * ri;
+      z[k] = zi;
+      rz = fma_(ri, zi, rz);
     }
+  };
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    VT pv[4], qv[4], xv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = i + u * stride;
+      pv[u] = p[k]; qv[u] = q[k]; xv[u] = x[k]; rv[u] = r[k];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) one(i + u * stride, pv[u], qv[u], xv[u], rv[u]);
   }
-  double v[2] = {rr, rz}, t[2];
-  if (grid_reduce<kBlock, 2>(v, t, partial, ticket) && threadIdx.x == 0) {
-    cg->rr = t[0];
-    cg->iters += 1;
-    if (t[0] <= cg->tol2 || cg->iters >= max_iter || !isfinite(t[0])) cg->done = 1;
-    if (JACOBI) {
+  for (; i < n; i += stride) one(i, p[i], q[i], x[i], r[i]);
+  if (JACOBI) {
+    double v[2] = {to_d(rr), to_d(rz)}, t[2];
+    if (grid_reduce<kBlock, 2>(v, t, partial, ticket) && threadIdx.x == 0) {
+      cg->rr = t[0];
+      cg->iters += 1;
+      if (t[0] <= cg->tol2 || cg->iters >= max_iter || !isfinite(t[0])) cg->done = 1;
       cg->beta = t[1] / cg->rz;
       cg->rz = t[1];
     }
+  } else {
+    double v[1] = {to_d(rr)}, t[1];
+    if (grid_reduce<kBlock, 1>(v, t, partial, ticket) && threadIdx.x == 0) {
+      cg->rr = t[0];
+      cg->iters += 1;
+      if (t[0] <= cg->tol2 || cg->iters >= max_iter || !isfinite(t[0])) cg->done = 1;
+    }
   }
 }
 
-// FSAI apply, first half: t = G r over entries up to the diagonal
-template <int TPR, typename PT, typename VT>
+// y = A x (FSAI first half: t = G r)
+template <typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock)
-fsai_lower_kernel(int64_t n, const int32_t* __restrict__ rowptr,
-                  const int32_t* __restrict__ dpos, const int32_t* __restrict__ col,
-                  const PT* __restrict__ g, const VT* __restrict__ r,
-                  VT* __restrict__ t, const CgScalars* cg) {
+sell_apply_kernel(SellArg<MT> A, const VT* __restrict__ x, VT* __restrict__ y,
+                  const CgScalars* cg) {
   if (*(volatile const int*)&cg->done) return;
-  const int lir = threadIdx.x % TPR;
-  const int64_t groups = (int64_t)gridDim.x * (kBlock / TPR);
-  for (int64_t i = blockIdx.x * (int64_t)(kBlock / TPR) + threadIdx.x / TPR;
-       i - (int64_t)(threadIdx.x / TPR) < n; i += groups) {
-    const bool ok = i < n;
-    const int32_t k0 = ok ? rowptr[i] : 0, k1 = ok ? dpos[i] + 1 : 0;
-    VT s = row_sum<TPR>(lir, k0, k1, col, g, r);
-    if (ok && lir == 0) t[i] = s;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (kBlock / 32);
+  for (int64_t s = blockIdx.x * (int64_t)(kBlock / 32) + (threadIdx.x >> 5);
+       s < A.nslices; s += warps) {
+    const int32_t r = __ldg(A.perm + 32 * s + lane);
+    const VT acc = sell_row(A, s, lane, x);
+    if (r >= 0) y[r] = acc;
   }
 }
 
-// FSAI apply, second half: z = G^T t over entries from the diagonal on,
-// r.z, then beta = (r.z)_new / (r.z)_old.  `init` keeps beta = 0.
-template <int TPR, typename PT, typename VT>
+// z = A t (FSAI second half: z = G^T t), r.z, then beta = (r.z)_new /
+// (r.z)_old.  `init` keeps beta = 0.
+template <typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock)
-fsai_upper_kernel(int64_t n, const int32_t* __restrict__ rowptr,
-                  const int32_t* __restrict__ dpos, const int32_t* __restrict__ col,
-                  const PT* __restrict__ g, const VT* __restrict__ t,
-                  const VT* __restrict__ r, VT* __restrict__ z, int init,
-                  CgScalars* cg, double* partial, unsigned* ticket) {
+sell_apply_dot_kernel(SellArg<MT> A, const VT* __restrict__ t,
+                      const VT* __restrict__ r, VT* __restrict__ z, int init,
+                      CgScalars* cg, double* partial, unsigned* ticket) {
   if (*(volatile int*)&cg->done) return;
-  const int lir = threadIdx.x % TPR;
-  const int64_t groups = (int64_t)gridDim.x * (kBlock / TPR);
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (kBlock / 32);
   double rz = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)(kBlock / TPR) + threadIdx.x / TPR;
-       i - (int64_t)(threadIdx.x / TPR) < n; i += groups) {
-    const bool ok = i < n;
-    const int32_t k0 = ok ? dpos[i] : 0, k1 = ok ? rowptr[i + 1] : 0;
-    VT s = row_sum<TPR>(lir, k0, k1, col, g, t);
-    if (ok && lir == 0) {
-      z[i] = s;
-      rz += to_d(r[i]) * to_d(s);
+  for (int64_t s = blockIdx.x * (int64_t)(kBlock / 32) + (threadIdx.x >> 5);
+       s < A.nslices; s += warps) {
+    const int32_t row = __ldg(A.perm + 32 * s + lane);
+    const VT acc = sell_row(A, s, lane, t);
+    if (row >= 0) {
+      z[row] = acc;
+      rz += to_d(r[row]) * to_d(acc);
     }
   }
   double v[1] = {rz}, tt[1];
@@ -202,11 +241,12 @@ fsai_upper_kernel(int64_t n, const int32_t* __restrict__ rowptr,
   }
 }
 
-// Jacobi at (re)start: z = dinv r, r.z
+// Jacobi at a (re)start: z = dinv r, r.z; `init` sets beta = 0, otherwise
+// beta = (r.z)_new / (r.z)_old keeps the search direction
 template <typename VT, typename DT>
 __global__ void __launch_bounds__(kBlock)
 jacobi_init_kernel(int64_t n, const DT* __restrict__ dinv, const VT* __restrict__ r,
-                   VT* __restrict__ z, CgScalars* cg, double* partial,
+                   VT* __restrict__ z, int init, CgScalars* cg, double* partial,
                    unsigned* ticket) {
   if (*(volatile int*)&cg->done) return;
   double rz = 0.0;
@@ -218,9 +258,19 @@ jacobi_init_kernel(int64_t n, const DT* __restrict__ dinv, const VT* __restrict_
   }
   double v[1] = {rz}, t[1];
   if (grid_reduce<kBlock, 1>(v, t, partial, ticket) && threadIdx.x == 0) {
-    cg->beta = 0.0;
+    cg->beta = init ? 0.0 : t[0] / cg->rz;
     cg->rz = t[0];
   }
+}
+
+// Start a new segment of the FP32 iteration after a reliable update: stop
+// again once r.r has dropped by `delta2` from the new (FP64) residual.
+__global__ void segment_kernel(CgScalars* cg, const double* rr64, double delta2,
+                               int restart) {
+  cg->tol2 = delta2 * *rr64;
+  cg->rr = *rr64;
+  cg->done = 0;
+  if (restart) cg->breakdown = 0;
 }
 
 // p = z + beta p
@@ -230,31 +280,35 @@ xpay_kernel(int64_t n, const VT* __restrict__ z, VT* __restrict__ p,
             const CgScalars* cg) {
   if (*(volatile const int*)&cg->done) return;
   const VT beta = (VT)cg->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    VT zv[4], pv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { zv[u] = z[i + u * stride]; pv[u] = p[i + u * stride]; }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[i + u * stride] = fma_(beta, pv[u], zv[u]);
+  }
+  for (; i < n; i += stride) p[i] = fma_(beta, p[i], z[i]);
 }
 
 // FP64 residual r = b - A x, r.r into *out; optionally r32 = (float) r
-template <int TPR>
 __global__ void __launch_bounds__(kBlock)
-residual_kernel(int64_t n, const int32_t* __restrict__ rowptr,
-                const int32_t* __restrict__ col, const double* __restrict__ val,
-                const double* __restrict__ x, const double* __restrict__ b,
-                double* __restrict__ r, float* __restrict__ r32, double* out,
-                double* partial, unsigned* ticket) {
-  const int lir = threadIdx.x % TPR;
-  const int64_t groups = (int64_t)gridDim.x * (kBlock / TPR);
+residual_kernel(SellArg<double> A, const double* __restrict__ x,
+                const double* __restrict__ b, double* __restrict__ r,
+                float* __restrict__ r32, double* out, double* partial,
+                unsigned* ticket) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (kBlock / 32);
   double rr = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)(kBlock / TPR) + threadIdx.x / TPR;
-       i - (int64_t)(threadIdx.x / TPR) < n; i += groups) {
-    const bool ok = i < n;
-    const int32_t k0 = ok ? rowptr[i] : 0, k1 = ok ? rowptr[i + 1] : 0;
-    double s = row_sum<TPR>(lir, k0, k1, col, val, x);
-    if (ok && lir == 0) {
-      double ri = b[i] - s;
-      r[i] = ri;
-      if (r32) r32[i] = (float)ri;
+  for (int64_t s = blockIdx.x * (int64_t)(kBlock / 32) + (threadIdx.x >> 5);
+       s < A.nslices; s += warps) {
+    const int32_t row = __ldg(A.perm + 32 * s + lane);
+    const double acc = sell_row(A, s, lane, x);
+    if (row >= 0) {
+      const double ri = b[row] - acc;
+      r[row] = ri;
+      if (r32) r32[row] = (float)ri;
       rr += ri * ri;
     }
   }
@@ -262,12 +316,14 @@ residual_kernel(int64_t n, const int32_t* __restrict__ rowptr,
   if (grid_reduce<kBlock, 1>(v, t, partial, ticket) && threadIdx.x == 0) *out = t[0];
 }
 
-// x64 += e32
+// x64 += e32, e32 = 0
 __global__ void __launch_bounds__(kBlock)
-correct_kernel(int64_t n, double* __restrict__ x, const float* __restrict__ e) {
+correct_kernel(int64_t n, double* __restrict__ x, float* __restrict__ e) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += (double)e[i];
+    e[i] = 0.0f;
+  }
 }
 
 // T = u + T0 on Dirichlet nodes
@@ -318,61 +374,59 @@ k_eff_kernel(int64_t n, const int32_t* __restrict__ rowptr,
 }
 
 // ------------------------------------------------------------- driver
-constexpr int kTpr = 8;          // lanes per CSR row (rows average ~16 nnz)
-constexpr int kTprHalf = 4;      // lanes per half row (FSAI factor)
 constexpr int kChunk = 16;       // iterations per graph launch / host poll
 
-struct Bufs {
-  // one precision's PCG vectors
-  void *x, *r, *z, *p, *q, *t;
+// Operators of one precision: L, the two FSAI halves (or Jacobi).
+template <typename MT, typename PT, typename DT>
+struct Ops {
+  SellArg<MT> A;
+  SellArg<PT> Glo, Gup;
+  const DT* dinv;
 };
 
 template <typename VT, typename MT, typename PT, typename DT>
-static void launch_iterations(dec_ctx* ctx, int64_t n, const MT* val,
-                              const PT* g, const DT* dinv, VT* x, VT* r, VT* z,
-                              VT* p, VT* q, VT* t, int max_iter, int count) {
+static void launch_iterations(dec_ctx* ctx, int64_t n, const Ops<MT, PT, DT>& op,
+                              VT* x, VT* r, VT* z, VT* p, VT* q, VT* t, int max_iter,
+                              int count) {
   cudaStream_t s = ctx->stream;
-  const unsigned G = (unsigned)ctx->reduce_grid;
+  const unsigned G = (unsigned)ctx->grid_vec, Gs = (unsigned)ctx->grid_sell;
   CgScalars* cg = ctx->cg.p;
   double* part = ctx->partial.p;
   unsigned* tk = ctx->ticket.p;
   const bool jac = ctx->precond == DEC_PRECOND_JACOBI;
   ctx->launches += (int64_t)count * (jac ? 3 : 5);
   for (int it = 0; it < count; ++it) {
-    spmv_pq_kernel<kTpr, MT, VT><<<G, kBlock, 0, s>>>(n, ctx->rowptr.p, ctx->col.p,
-                                                     val, p, q, cg, part, tk);
+    spmv_pq_kernel<MT, VT><<<Gs, kBlock, 0, s>>>(op.A, p, q, cg, part, tk);
     if (jac) {
-      update_kernel<VT, DT, true><<<G, kBlock, 0, s>>>(n, x, r, p, q, dinv, z,
+      update_kernel<VT, DT, true><<<G, kBlock, 0, s>>>(n, x, r, p, q, op.dinv, z,
                                                        max_iter, cg, part, tk);
     } else {
-      update_kernel<VT, DT, false><<<G, kBlock, 0, s>>>(n, x, r, p, q, dinv, z,
+      update_kernel<VT, DT, false><<<G, kBlock, 0, s>>>(n, x, r, p, q, op.dinv, z,
                                                         max_iter, cg, part, tk);
-      fsai_lower_kernel<kTprHalf, PT, VT><<<G, kBlock, 0, s>>>(
-          n, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, g, r, t, cg);
-      fsai_upper_kernel<kTprHalf, PT, VT><<<G, kBlock, 0, s>>>(
-          n, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, g, t, r, z, 0, cg, part, tk);
+      sell_apply_kernel<PT, VT><<<Gs, kBlock, 0, s>>>(op.Glo, r, t, cg);
+      sell_apply_dot_kernel<PT, VT><<<Gs, kBlock, 0, s>>>(op.Gup, t, r, z, 0, cg, part, tk);
     }
     xpay_kernel<VT><<<G, kBlock, 0, s>>>(n, z, p, cg);
   }
 }
 
-// (Re)start: given r, compute z = M r, r.z, and p = z.
-template <typename VT, typename PT, typename DT>
-static void launch_restart(dec_ctx* ctx, int64_t n, const PT* g, const DT* dinv,
-                           VT* r, VT* z, VT* p, VT* t) {
+// (Re)start from the current r: z = M r, r.z and p = z (init) or, after a
+// reliable update that keeps the search direction, p = z + beta p with
+// beta = (r.z)_new / (r.z)_old.
+template <typename VT, typename MT, typename PT, typename DT>
+static void launch_restart(dec_ctx* ctx, int64_t n, const Ops<MT, PT, DT>& op, VT* r,
+                           VT* z, VT* p, VT* t, int init = 1) {
   cudaStream_t s = ctx->stream;
-  const unsigned G = (unsigned)ctx->reduce_grid;
+  const unsigned G = (unsigned)ctx->grid_vec, Gs = (unsigned)ctx->grid_sell;
   CgScalars* cg = ctx->cg.p;
   ctx->launches += ctx->precond == DEC_PRECOND_JACOBI ? 2 : 3;
   if (ctx->precond == DEC_PRECOND_JACOBI) {
-    jacobi_init_kernel<VT, DT><<<G, kBlock, 0, s>>>(n, dinv, r, z, cg, ctx->partial.p,
-                                                    ctx->ticket.p);
+    jacobi_init_kernel<VT, DT><<<G, kBlock, 0, s>>>(n, op.dinv, r, z, init, cg,
+                                                    ctx->partial.p, ctx->ticket.p);
   } else {
-    fsai_lower_kernel<kTprHalf, PT, VT><<<G, kBlock, 0, s>>>(
-        n, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, g, r, t, cg);
-    fsai_upper_kernel<kTprHalf, PT, VT><<<G, kBlock, 0, s>>>(
-        n, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, g, t, r, z, 1, cg,
-        ctx->partial.p, ctx->ticket.p);
+    sell_apply_kernel<PT, VT><<<Gs, kBlock, 0, s>>>(op.Glo, r, t, cg);
+    sell_apply_dot_kernel<PT, VT><<<Gs, kBlock, 0, s>>>(op.Gup, t, r, z, init, cg,
+                                                       ctx->partial.p, ctx->ticket.p);
   }
   xpay_kernel<VT><<<G, kBlock, 0, s>>>(n, z, p, cg);
 }
@@ -386,22 +440,21 @@ static dec_status read_cg(dec_ctx* ctx, CgScalars* h) {
 
 // Run chunks of iterations (one captured graph per chunk) until `done`.
 template <typename VT, typename MT, typename PT, typename DT>
-static dec_status run_pcg(dec_ctx* ctx, int64_t n, const MT* val, const PT* g,
-                          const DT* dinv, VT* x, VT* r, VT* z, VT* p, VT* q, VT* t,
-                          int max_iter, CgScalars* h) {
+static dec_status run_pcg(dec_ctx* ctx, int64_t n, const Ops<MT, PT, DT>& op, VT* x,
+                          VT* r, VT* z, VT* p, VT* q, VT* t, int max_iter,
+                          CgScalars* h) {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  const int64_t per_chunk = (int64_t)kChunk * (ctx->precond == DEC_PRECOND_JACOBI ? 3 : 5);
   DEC_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-  launch_iterations<VT, MT, PT, DT>(ctx, n, val, g, dinv, x, r, z, p, q, t, max_iter,
-                                    kChunk);
+  launch_iterations<VT, MT, PT, DT>(ctx, n, op, x, r, z, p, q, t, max_iter, kChunk);
+  ctx->launches -= per_chunk;  // counted per replay below
   cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
   if (ce != cudaSuccess) return ctx->cuda_fail(ce, "cudaStreamEndCapture");
   ce = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (ce != cudaSuccess) return ctx->cuda_fail(ce, "cudaGraphInstantiate");
   dec_status st = DEC_OK;
-  const int64_t per_chunk = (int64_t)kChunk * (ctx->precond == DEC_PRECOND_JACOBI ? 3 : 5);
-  ctx->launches -= per_chunk;  // capture itself launches nothing
   for (;;) {
     ctx->launches += per_chunk;
     ce = cudaGraphLaunch(exec, ctx->stream);
@@ -415,11 +468,11 @@ static dec_status run_pcg(dec_ctx* ctx, int64_t n, const MT* val, const PT* g,
 
 dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
                           int mode, int* iters_out, double* relres_out) {
-  const int64_t n = ctx->n, nnz = ctx->nnz;
+  const int64_t n = ctx->n;
   const int vs = ctx->n_scales > 1 ? inst : 0;
   cudaStream_t s = ctx->stream;
-  const unsigned G = (unsigned)ctx->reduce_grid;
-  const double* val64 = ctx->val64.p + (int64_t)vs * nnz;
+  const unsigned G = (unsigned)ctx->grid_vec, Gs = (unsigned)ctx->grid_sell;
+  const SellArg<double> A64 = sell_arg(ctx->sellL, ctx->sL64.p + (int64_t)vs * ctx->sellL.total);
   const double* bvec = ctx->b.p + (int64_t)inst * n;
   double* u = ctx->u.p + (int64_t)inst * n;
   CgScalars h{};
@@ -427,30 +480,32 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
   double rr_true = 0.0, bnorm2 = 0.0;
   int total_iters = 0;
   dec_status st = DEC_OK;
+  const bool fsai = ctx->precond == DEC_PRECOND_FSAI;
 
   if (mode == DEC_MODE_FP64) {
-    const double* g = ctx->g64.p + (int64_t)vs * nnz;
-    const double* dinv = ctx->dinv64.p + (int64_t)vs * n;
+    Ops<double, double, double> op{
+        A64,
+        sell_arg(ctx->sellLo, fsai ? ctx->sGlo64.p + (int64_t)vs * ctx->sellLo.total : nullptr),
+        sell_arg(ctx->sellUp, fsai ? ctx->sGup64.p + (int64_t)vs * ctx->sellUp.total : nullptr),
+        fsai ? nullptr : ctx->dinv64.p + (int64_t)vs * n};
     double *x = ctx->x64.p, *r = ctx->r64.p, *z = ctx->z64.p, *p = ctx->p64.p,
            *q = ctx->q64.p, *t = ctx->t64.p;
     ctx->launches += 1;
     cg_init_kernel<double, double><<<G, kBlock, 0, s>>>(n, bvec, x, r, p, rtol * rtol,
                                                         ctx->cg.p, ctx->partial.p,
                                                         ctx->ticket.p);
-    launch_restart<double, double, double>(ctx, n, g, dinv, r, z, p, t);
+    launch_restart<double>(ctx, n, op, r, z, p, t);
     DEC_TRY(cudaGetLastError());
     for (;;) {
-      st = run_pcg<double, double, double, double>(ctx, n, val64, g, dinv, x, r, z, p,
-                                                   q, t, max_iter, &h);
+      st = run_pcg<double>(ctx, n, op, x, r, z, p, q, t, max_iter, &h);
       if (st != DEC_OK) return st;
       bnorm2 = h.bnorm2;
       total_iters = h.iters;
       if (bnorm2 == 0.0) { rr_true = 0.0; break; }
       // true residual, replacing the recursive one
       ctx->launches += 1;
-      residual_kernel<kTpr><<<G, kBlock, 0, s>>>(n, ctx->rowptr.p, ctx->col.p, val64,
-                                                x, bvec, r, nullptr, rr_dev,
-                                                ctx->partial.p, ctx->ticket.p);
+      residual_kernel<<<Gs, kBlock, 0, s>>>(A64, x, bvec, r, nullptr, rr_dev, ctx->partial.p,
+                                           ctx->ticket.p);
       DEC_TRY(cudaMemcpyAsync(&rr_true, rr_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
       DEC_TRY(cudaStreamSynchronize(s));
       if (h.breakdown) { st = ctx->fail(DEC_ERR_BREAKDOWN, "CG breakdown: p.Lp <= 0 or not finite"); break; }
@@ -459,56 +514,62 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
       // restart from the true residual
       int zero = 0;
       DEC_TRY(cudaMemcpyAsync(&ctx->cg.p->done, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
-      launch_restart<double, double, double>(ctx, n, g, dinv, r, z, p, t);
+      launch_restart<double>(ctx, n, op, r, z, p, t);
       DEC_TRY(cudaGetLastError());
     }
     DEC_TRY(cudaMemcpyAsync(u, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   } else {
-    // mixed: FP64 defect correction around FP32 PCG
-    const float* val32 = ctx->val32.p + (int64_t)vs * nnz;
-    const __nv_bfloat16* g = ctx->g16.p + (int64_t)vs * nnz;
-    const float* dinv = ctx->dinv32.p + (int64_t)vs * n;
+    // Mixed: one FP32 PCG whose residual is replaced, every time it has
+    // dropped by kSegment since the last replacement, by the FP64 residual
+    // b - L x of the FP64 solution x += (FP32 accumulated update) ("reliable
+    // updates": defect correction that keeps the search direction, so the
+    // iteration count stays close to FP64 CG).  Convergence is decided on
+    // the FP64 residual only.
+    Ops<float, __nv_bfloat16, float> op{
+        sell_arg(ctx->sellL, ctx->sL32.p + (int64_t)vs * ctx->sellL.total),
+        sell_arg(ctx->sellLo, fsai ? ctx->sGlo16.p + (int64_t)vs * ctx->sellLo.total : nullptr),
+        sell_arg(ctx->sellUp, fsai ? ctx->sGup16.p + (int64_t)vs * ctx->sellUp.total : nullptr),
+        fsai ? nullptr : ctx->dinv32.p + (int64_t)vs * n};
+    constexpr double kSegment = 1e-4;   // r.r drop between replacements (1e-2 in norm)
     double* x64 = ctx->x64.p;
     double* r64 = ctx->r64.p;
     float *x = ctx->x32.p, *r = ctx->r32.p, *z = ctx->z32.p, *p = ctx->p32.p,
           *q = ctx->q32.p, *t = ctx->t32.p;
     DEC_TRY(cudaMemsetAsync(x64, 0, sizeof(double) * n, s));
-    // r64 = b - L*0 = b, r32 = (float) b, |b|^2
-    ctx->launches += 1;
-    residual_kernel<kTpr><<<G, kBlock, 0, s>>>(n, ctx->rowptr.p, ctx->col.p, val64, x64,
-                                              bvec, r64, ctx->t32.p, rr_dev,
-                                              ctx->partial.p, ctx->ticket.p);
+    // r64 = b, r32 = (float) b, |b|^2; the FP32 state starts from r32
+    ctx->launches += 2;
+    residual_kernel<<<Gs, kBlock, 0, s>>>(A64, x64, bvec, r64, q, rr_dev, ctx->partial.p,
+                                         ctx->ticket.p);
+    cg_init_kernel<float, float><<<G, kBlock, 0, s>>>(n, q, x, r, p, kSegment, ctx->cg.p,
+                                                      ctx->partial.p, ctx->ticket.p);
     DEC_TRY(cudaMemcpyAsync(&bnorm2, rr_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    launch_restart<float>(ctx, n, op, r, z, p, t, 1);
+    DEC_TRY(cudaGetLastError());
     DEC_TRY(cudaStreamSynchronize(s));
     rr_true = bnorm2;
-    const double inner_rtol = 1e-4;
     double best = rr_true;
     int stall = 0;
     while (bnorm2 > 0.0 && rr_true > rtol * rtol * bnorm2) {
-      if (total_iters >= max_iter) { st = ctx->fail(DEC_NOT_CONVERGED, "max_iter reached"); break; }
-      ctx->launches += 3;  // init, correction, residual
-      cg_init_kernel<float, float><<<G, kBlock, 0, s>>>(n, ctx->t32.p, x, r, p,
-                                                        inner_rtol * inner_rtol,
-                                                        ctx->cg.p, ctx->partial.p,
-                                                        ctx->ticket.p);
-      launch_restart<float, __nv_bfloat16, float>(ctx, n, g, dinv, r, z, p, t);
-      DEC_TRY(cudaGetLastError());
-      st = run_pcg<float, float, __nv_bfloat16, float>(ctx, n, val32, g, dinv, x, r, z,
-                                                       p, q, t, max_iter - total_iters, &h);
+      st = run_pcg<float>(ctx, n, op, x, r, z, p, q, t, max_iter, &h);
       if (st != DEC_OK) return st;
-      total_iters += h.iters;
+      total_iters = h.iters;
+      // reliable update: x64 += x32, x32 = 0, r64 = b - L x64, r32 = (float) r64
+      ctx->launches += 2;
       correct_kernel<<<G, kBlock, 0, s>>>(n, x64, x);
-      residual_kernel<kTpr><<<G, kBlock, 0, s>>>(n, ctx->rowptr.p, ctx->col.p, val64,
-                                                x64, bvec, r64, ctx->t32.p, rr_dev,
-                                                ctx->partial.p, ctx->ticket.p);
+      residual_kernel<<<Gs, kBlock, 0, s>>>(A64, x64, bvec, r64, r, rr_dev, ctx->partial.p,
+                                           ctx->ticket.p);
       DEC_TRY(cudaMemcpyAsync(&rr_true, rr_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
       DEC_TRY(cudaStreamSynchronize(s));
-      if (h.breakdown && !(rr_true < best)) {
-        st = ctx->fail(DEC_ERR_BREAKDOWN, "CG breakdown in the FP32 inner solve");
-        break;
-      }
-      if (rr_true < 0.25 * best) { best = rr_true; stall = 0; }
-      else if (++stall >= 3) { st = ctx->fail(DEC_NOT_CONVERGED, "defect correction stalled"); break; }
+      if (rr_true <= rtol * rtol * bnorm2) break;
+      if (h.iters >= max_iter) { st = ctx->fail(DEC_NOT_CONVERGED, "max_iter reached"); break; }
+      if (rr_true < 0.5 * best) { best = rr_true; stall = 0; }
+      else if (++stall >= 4) { st = ctx->fail(DEC_NOT_CONVERGED, "residual replacement stalled"); break; }
+      // next segment; after a breakdown or a stall restart the direction too
+      const int restart = (h.breakdown || stall > 0) ? 1 : 0;
+      ctx->launches += 1;
+      segment_kernel<<<1, 1, 0, s>>>(ctx->cg.p, rr_dev, kSegment, restart);
+      launch_restart<float>(ctx, n, op, r, z, p, t, restart);
+      DEC_TRY(cudaGetLastError());
     }
     DEC_TRY(cudaMemcpyAsync(u, x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   }
@@ -520,7 +581,7 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
 dec_status k_eff_instance(dec_ctx* ctx, int inst, double* out3_host) {
   const int64_t n = ctx->n;
   cudaStream_t s = ctx->stream;
-  const unsigned G = (unsigned)ctx->reduce_grid;
+  const unsigned G = (unsigned)ctx->grid_vec;
   const int ts = ctx->n_sets > 1 ? inst : 0;
   double* T = ctx->t64.p;  // scratch
   ctx->launches += 2;
@@ -541,30 +602,25 @@ dec_status k_eff_instance(dec_ctx* ctx, int inst, double* out3_host) {
 dec_status form_T(dec_ctx* ctx, int inst, double* T) {
   const int ts = ctx->n_sets > 1 ? inst : 0;
   ctx->launches += 1;
-  form_T_kernel<<<(unsigned)ctx->reduce_grid, kBlock, 0, ctx->stream>>>(
+  form_T_kernel<<<(unsigned)ctx->grid_vec, kBlock, 0, ctx->stream>>>(
       ctx->n, ctx->u.p + (int64_t)inst * ctx->n, ctx->T0.p + (int64_t)ts * ctx->n,
       ctx->tag.p, T);
   DEC_TRY(cudaGetLastError());
   return DEC_OK;
 }
 
-}  // namespace dec
-
-namespace dec {
-
-// Time `reps` launches of one solver kernel on the current instance's data,
-// each preceded (outside the timed events) by a write of `flush_bytes` to
-// evict L2, so the figure is the HBM-bound duration of a launch.
+// Time `reps` launches of one solver kernel on instance 0's data, each
+// preceded (outside the timed events) by a write of `flush_bytes` to evict
+// L2, so the figure is the cold-cache duration of a launch.
 dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
                        double* avg_ms) {
   const int64_t n = ctx->n;
   cudaStream_t s = ctx->stream;
-  const unsigned G = (unsigned)ctx->reduce_grid;
+  const unsigned G = (unsigned)ctx->grid_sell;
   DEC_TRY(ctx->flush.ensure(flush_bytes > 0 ? flush_bytes : 1));
-  for (auto* bf : {&ctx->p64, &ctx->q64, &ctx->t64, &ctx->z64}) DEC_TRY(bf->ensure(n));
+  for (auto* bf : {&ctx->p64, &ctx->q64, &ctx->t64, &ctx->z64, &ctx->r64}) DEC_TRY(bf->ensure(n));
   for (auto* bf : {&ctx->p32, &ctx->q32, &ctx->t32, &ctx->z32, &ctx->r32}) DEC_TRY(bf->ensure(n));
-  DEC_TRY(ctx->r64.ensure(n));
-  // finite operands: p = b (and its FP32 copy), done = 0
+  // finite operands: p = r = b (FP64), zeros (FP32), done = 0
   DEC_TRY(cudaMemcpyAsync(ctx->p64.p, ctx->b.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   DEC_TRY(cudaMemcpyAsync(ctx->r64.p, ctx->b.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   DEC_TRY(cudaMemsetAsync(ctx->p32.p, 0, sizeof(float) * n, s));
@@ -572,44 +628,51 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
   CgScalars h{};
   h.rz = 1.0;
   DEC_TRY(cudaMemcpyAsync(ctx->cg.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  const auto L64 = sell_arg(ctx->sellL, ctx->sL64.p);
+  const auto L32 = sell_arg(ctx->sellL, ctx->sL32.p);
+  const auto Glo64 = sell_arg(ctx->sellLo, ctx->sGlo64.p);
+  const auto Gup64 = sell_arg(ctx->sellUp, ctx->sGup64.p);
+  const auto Glo16 = sell_arg(ctx->sellLo, ctx->sGlo16.p);
+  const auto Gup16 = sell_arg(ctx->sellUp, ctx->sGup16.p);
   cudaEvent_t e0, e1;
   DEC_TRY(cudaEventCreate(&e0));
   DEC_TRY(cudaEventCreate(&e1));
   double total = 0.0;
-  for (int it = 0; it < reps; ++it) {
+  dec_status st = DEC_OK;
+  for (int it = 0; it < reps && st == DEC_OK; ++it) {
     if (flush_bytes) DEC_TRY(cudaMemsetAsync(ctx->flush.p, it & 0xff, flush_bytes, s));
     DEC_TRY(cudaMemcpyAsync(&ctx->cg.p->done, &h.done, sizeof(int), cudaMemcpyHostToDevice, s));
     DEC_TRY(cudaEventRecord(e0, s));
     switch (which) {
       case DEC_KERNEL_SPMV_F64:
-        spmv_pq_kernel<kTpr, double, double><<<G, kBlock, 0, s>>>(
-            n, ctx->rowptr.p, ctx->col.p, ctx->val64.p, ctx->p64.p, ctx->q64.p, ctx->cg.p,
-            ctx->partial.p, ctx->ticket.p);
+        spmv_pq_kernel<double, double><<<G, kBlock, 0, s>>>(L64, ctx->p64.p, ctx->q64.p,
+                                                            ctx->cg.p, ctx->partial.p,
+                                                            ctx->ticket.p);
         break;
       case DEC_KERNEL_SPMV_F32:
-        spmv_pq_kernel<kTpr, float, float><<<G, kBlock, 0, s>>>(
-            n, ctx->rowptr.p, ctx->col.p, ctx->val32.p, ctx->p32.p, ctx->q32.p, ctx->cg.p,
-            ctx->partial.p, ctx->ticket.p);
+        spmv_pq_kernel<float, float><<<G, kBlock, 0, s>>>(L32, ctx->p32.p, ctx->q32.p,
+                                                          ctx->cg.p, ctx->partial.p,
+                                                          ctx->ticket.p);
         break;
       case DEC_KERNEL_FSAI_F64:
-        fsai_lower_kernel<kTprHalf, double, double><<<G, kBlock, 0, s>>>(
-            n, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, ctx->g64.p, ctx->r64.p, ctx->t64.p, ctx->cg.p);
-        fsai_upper_kernel<kTprHalf, double, double><<<G, kBlock, 0, s>>>(
-            n, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, ctx->g64.p, ctx->t64.p, ctx->r64.p,
-            ctx->z64.p, 1, ctx->cg.p, ctx->partial.p, ctx->ticket.p);
+        sell_apply_kernel<double, double><<<G, kBlock, 0, s>>>(Glo64, ctx->r64.p, ctx->t64.p,
+                                                               ctx->cg.p);
+        sell_apply_dot_kernel<double, double><<<G, kBlock, 0, s>>>(
+            Gup64, ctx->t64.p, ctx->r64.p, ctx->z64.p, 1, ctx->cg.p, ctx->partial.p,
+            ctx->ticket.p);
         break;
       case DEC_KERNEL_FSAI_BF16:
-        fsai_lower_kernel<kTprHalf, __nv_bfloat16, float><<<G, kBlock, 0, s>>>(
-            n, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, ctx->g16.p, ctx->r32.p, ctx->t32.p, ctx->cg.p);
-        fsai_upper_kernel<kTprHalf, __nv_bfloat16, float><<<G, kBlock, 0, s>>>(
-            n, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, ctx->g16.p, ctx->t32.p, ctx->r32.p,
-            ctx->z32.p, 1, ctx->cg.p, ctx->partial.p, ctx->ticket.p);
+        sell_apply_kernel<__nv_bfloat16, float><<<G, kBlock, 0, s>>>(
+            Glo16, ctx->r32.p, ctx->t32.p, ctx->cg.p);
+        sell_apply_dot_kernel<__nv_bfloat16, float><<<G, kBlock, 0, s>>>(
+            Gup16, ctx->t32.p, ctx->r32.p, ctx->z32.p, 1, ctx->cg.p, ctx->partial.p,
+            ctx->ticket.p);
         break;
       default:
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return ctx->fail(DEC_ERR_ARG, "time_kernel: unknown kernel id");
+        st = ctx->fail(DEC_ERR_ARG, "time_kernel: unknown kernel id");
+        continue;
     }
+    ctx->launches += (which >= DEC_KERNEL_FSAI_F64) ? 2 : 1;
     DEC_TRY(cudaEventRecord(e1, s));
     DEC_TRY(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -618,8 +681,8 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  *avg_ms = total / reps;
-  return DEC_OK;
+  if (st == DEC_OK) *avg_ms = total / reps;
+  return st;
 }
 
 }  // namespace dec

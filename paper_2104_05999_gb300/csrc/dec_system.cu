@@ -22,15 +22,12 @@ __global__ void laplacian_values_kernel(
     const int32_t* __restrict__ eid, const int32_t* __restrict__ dpos,
     const uint8_t* __restrict__ tag, const double* __restrict__ w,
     const uint8_t* __restrict__ fc, int state, const double* __restrict__ T0,
-    double* __restrict__ val, float* __restrict__ val32, double* __restrict__ b) {
+    double* __restrict__ val, double* __restrict__ b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k0 = rowptr[i], k1 = rowptr[i + 1], kd = dpos[i];
     if (tag[i] == DEC_NODE_DIRICHLET) {
-      for (int32_t k = k0; k < k1; ++k) {
-        val[k] = k == kd ? 1.0 : 0.0;
-        if (val32) val32[k] = k == kd ? 1.0f : 0.0f;
-      }
+      for (int32_t k = k0; k < k1; ++k) val[k] = k == kd ? 1.0 : 0.0;
       b[i] = 0.0;
       continue;
     }
@@ -48,15 +45,12 @@ __global__ void laplacian_values_kernel(
         v = we == 0.0 ? 0.0 : -we;
       }
       val[k] = v;
-      if (val32) val32[k] = (float)v;
     }
     if (diag == 0.0) {  // isolated by cracks: decoupled identity row
       val[kd] = 1.0;
-      if (val32) val32[kd] = 1.0f;
       b[i] = 0.0;
     } else {
       val[kd] = diag;
-      if (val32) val32[kd] = (float)diag;
       b[i] = bi;
     }
   }
@@ -126,20 +120,23 @@ __device__ bool fsai_cholesky(int lane, int k, double (*A)[kFsaiMax + 1],
   return true;
 }
 
+// Warp-per-row FSAI setup for the rows listed by the thread-per-row kernel
+// (k > kFsaiThread); rows with k > kFsaiMax raise error bit 8.
 __global__ void __launch_bounds__(32 * kFsaiWarps)
-fsai_setup_kernel(int64_t n, const int32_t* __restrict__ rowptr,
-                  const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
-                  const int32_t* __restrict__ dpos,
-                  const int32_t* __restrict__ pos_up,
-                  const double* __restrict__ val, double* __restrict__ g64,
-                  __nv_bfloat16* __restrict__ g16, int* errflag) {
+fsai_setup_list_kernel(const int32_t* __restrict__ rows, const int32_t* __restrict__ count,
+                       const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const int32_t* __restrict__ eid, const int32_t* __restrict__ dpos,
+                       const int32_t* __restrict__ pos_up, const double* __restrict__ val,
+                       double* __restrict__ g64, int* errflag) {
   __shared__ double Ash[kFsaiWarps][kFsaiMax][kFsaiMax + 1];
   __shared__ int32_t Psh[kFsaiWarps][kFsaiMax];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double (*A)[kFsaiMax + 1] = Ash[wid];
   int32_t* P = Psh[wid];
   const int64_t warps = (int64_t)gridDim.x * kFsaiWarps;
-  for (int64_t i = blockIdx.x * (int64_t)kFsaiWarps + wid; i < n; i += warps) {
+  const int64_t nrows = *count;
+  for (int64_t li = blockIdx.x * (int64_t)kFsaiWarps + wid; li < nrows; li += warps) {
+    const int64_t i = rows[li];
     const int32_t k0 = rowptr[i], kd = dpos[i];
     const int k = kd - k0 + 1;
     if (k > kFsaiMax) {
@@ -174,12 +171,101 @@ fsai_setup_kernel(int64_t n, const int32_t* __restrict__ rowptr,
     if (lane < k) {
       const int32_t pos = k0 + lane;
       g64[pos] = g;
-      if (g16) g16[pos] = __float2bfloat16_rn((float)g);
       if (lane < k - 1) {  // transpose slot: entry (P[lane], i) in row P[lane]
         const int32_t tp = pos_up[eid[pos]];
         g64[tp] = g;
-        if (g16) g16[tp] = __float2bfloat16_rn((float)g);
       }
+    }
+  }
+}
+
+// Thread-per-row FSAI setup for rows with k <= kFsaiThread: every FP64
+// instruction of a warp works on 32 rows (GB300's FP64 pipe is narrow, so
+// idle lanes cost as much as busy ones).  Each thread keeps the packed lower
+// triangle of its k x k block in shared memory, interleaved across threads
+// (element e of thread t at A[e * blockDim + t]) so that accesses do not
+// conflict.  Rows with k > kFsaiThread go to a list for the warp-per-row
+// kernel above.
+constexpr int kFsaiThread = 16;
+constexpr int kFsaiTpb = 64;
+constexpr int kPacked = kFsaiThread * (kFsaiThread + 1) / 2;
+
+__device__ __forceinline__ int tri(int a, int b) { return a * (a + 1) / 2 + b; }
+
+__device__ void fsai_gather_thread(int k, const int32_t* P, int stride,
+                                   const int32_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ dpos,
+                                   const int32_t* __restrict__ col,
+                                   const double* __restrict__ val, double* A,
+                                   double shift) {
+  for (int a = 0; a < k; ++a) {
+    for (int b = 0; b <= a; ++b) A[tri(a, b) * stride] = 0.0;
+    const int32_t r = P[a * stride];
+    // lower part of row r (columns <= r, sorted) merged with P[0..a]
+    int b = 0;
+    const int32_t kend = dpos[r];
+    for (int32_t kk = rowptr[r]; kk <= kend; ++kk) {
+      const int32_t c = col[kk];
+      while (b < a && P[b * stride] < c) ++b;
+      if (P[b * stride] == c) A[tri(a, b) * stride] = val[kk];
+    }
+    A[tri(a, a) * stride] += shift;
+  }
+}
+
+__device__ bool fsai_chol_thread(int k, double* A, int stride, double pivot_min) {
+  for (int c = 0; c < k; ++c) {
+    const double d = A[tri(c, c) * stride];
+    if (!(d > pivot_min)) return false;
+    const double lc = sqrt(d);
+    const double inv = 1.0 / lc;
+    A[tri(c, c) * stride] = lc;
+    for (int r = c + 1; r < k; ++r) A[tri(r, c) * stride] *= inv;
+    for (int r = c + 1; r < k; ++r) {
+      const double lrc = A[tri(r, c) * stride];
+      for (int q = c + 1; q <= r; ++q) A[tri(r, q) * stride] -= lrc * A[tri(q, c) * stride];
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kFsaiTpb)
+fsai_setup_thread_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                         const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
+                         const int32_t* __restrict__ dpos,
+                         const int32_t* __restrict__ pos_up,
+                         const double* __restrict__ val, double* __restrict__ g64,
+                         int32_t* __restrict__ big_rows, int32_t* __restrict__ big_count) {
+  extern __shared__ double smem[];
+  double* A = smem + threadIdx.x;                          // stride kFsaiTpb
+  int32_t* P = (int32_t*)(smem + kPacked * kFsaiTpb) + threadIdx.x;
+  const int stride = kFsaiTpb;
+  for (int64_t i = blockIdx.x * (int64_t)kFsaiTpb + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kFsaiTpb) {
+    const int32_t k0 = rowptr[i], kd = dpos[i];
+    const int k = kd - k0 + 1;
+    if (k > kFsaiThread) {
+      big_rows[atomicAdd(big_count, 1)] = (int32_t)i;
+      continue;
+    }
+    for (int a = 0; a < k; ++a) P[a * stride] = col[k0 + a];
+    fsai_gather_thread(k, P, stride, rowptr, dpos, col, val, A, 0.0);
+    double dmax = 0.0;
+    for (int a = 0; a < k; ++a) dmax = fmax(dmax, A[tri(a, a) * stride]);
+    if (!fsai_chol_thread(k, A, stride, kPivotRel * dmax)) {
+      fsai_gather_thread(k, P, stride, rowptr, dpos, col, val, A, kShiftRel * dmax);
+      fsai_chol_thread(k, A, stride, 0.0);
+    }
+    // C^T g = e_k, g_j stored over the used diagonal slot C_jj
+    for (int j = k - 1; j >= 0; --j) {
+      double sum = (j == k - 1) ? 1.0 : 0.0;
+      for (int r = j + 1; r < k; ++r) sum -= A[tri(r, j) * stride] * A[tri(r, r) * stride];
+      A[tri(j, j) * stride] = sum / A[tri(j, j) * stride];
+    }
+    for (int a = 0; a < k; ++a) {
+      const double g = A[tri(a, a) * stride];
+      g64[k0 + a] = g;
+      if (a < k - 1) g64[pos_up[eid[k0 + a]]] = g;
     }
   }
 }
@@ -190,44 +276,62 @@ static unsigned grid_rows(const dec_ctx* ctx, int64_t work, int per_block) {
   return (unsigned)std::max<int64_t>(1, std::min(g, cap));
 }
 
-dec_status build_values(dec_ctx* ctx, int inst, bool want32) {
+dec_status build_values(dec_ctx* ctx, int inst) {
   const int64_t n = ctx->n, nnz = ctx->nnz;
   const int vs = ctx->n_scales > 1 ? inst : 0;      // value set
   const int ts = ctx->n_sets > 1 ? inst : 0;        // Dirichlet set
   double* val = ctx->val64.p + (int64_t)vs * nnz;
-  float* v32 = want32 ? ctx->val32.p + (int64_t)vs * nnz : nullptr;
   laplacian_values_kernel<<<grid_rows(ctx, n, 256), 256, 0, ctx->stream>>>(
       n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->w.p,
       ctx->first_cut.p, ctx->n_scales > 1 ? inst : 0, ctx->T0.p + (int64_t)ts * n,
-      val, v32, ctx->b.p + (int64_t)inst * n);
+      val, ctx->b.p + (int64_t)inst * n);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 1;
+  if (inst == vs) {   // first instance of this value set: solver copies
+    const int64_t tot = ctx->sellL.total;
+    DEC_TRY_STATUS(scatter_values<double>(ctx, ctx->sellL, val, ctx->sL64.p + (int64_t)vs * tot));
+    DEC_TRY_STATUS(scatter_values<float>(ctx, ctx->sellL, val, ctx->sL32.p + (int64_t)vs * tot));
+  }
   return DEC_OK;
 }
 
-dec_status build_precond(dec_ctx* ctx, int inst, bool want16) {
+dec_status build_precond(dec_ctx* ctx, int vs) {
   const int64_t n = ctx->n, nnz = ctx->nnz;
-  const int vs = ctx->n_scales > 1 ? inst : 0;
   const double* val = ctx->val64.p + (int64_t)vs * nnz;
   cudaStream_t s = ctx->stream;
   if (ctx->precond == DEC_PRECOND_JACOBI) {
     jacobi_kernel<<<grid_rows(ctx, n, 256), 256, 0, s>>>(
-        n, ctx->dpos.p, val, ctx->dinv64.p + (int64_t)vs * n,
-        ctx->dinv32.p ? ctx->dinv32.p + (int64_t)vs * n : nullptr);
+        n, ctx->dpos.p, val, ctx->dinv64.p + (int64_t)vs * n, ctx->dinv32.p + (int64_t)vs * n);
     DEC_TRY(cudaGetLastError());
     ctx->launches += 1;
     return DEC_OK;
   }
+  double* g = ctx->g64.p + (int64_t)vs * nnz;
+  DEC_TRY(ctx->big_rows.ensure(n + 1));
+  int32_t* big_count = ctx->big_rows.p + n;
   DEC_TRY(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
-  fsai_setup_kernel<<<grid_rows(ctx, n, kFsaiWarps), 32 * kFsaiWarps, 0, s>>>(
-      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->pos_up.p, val,
-      ctx->g64.p + (int64_t)vs * nnz,
-      want16 ? ctx->g16.p + (int64_t)vs * nnz : nullptr, ctx->errflag.p);
+  DEC_TRY(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s));
+  const size_t smem = (size_t)kPacked * kFsaiTpb * sizeof(double) +
+                      (size_t)kFsaiThread * kFsaiTpb * sizeof(int32_t);
+  DEC_TRY(cudaFuncSetAttribute(fsai_setup_thread_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned gt = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((n + kFsaiTpb - 1) / kFsaiTpb, (int64_t)ctx->num_sms * 3));
+  fsai_setup_thread_kernel<<<gt, kFsaiTpb, smem, s>>>(
+      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->pos_up.p, val, g,
+      ctx->big_rows.p, big_count);
+  fsai_setup_list_kernel<<<(unsigned)ctx->num_sms, 32 * kFsaiWarps, 0, s>>>(
+      ctx->big_rows.p, big_count, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p,
+      ctx->pos_up.p, val, g, ctx->errflag.p);
   DEC_TRY(cudaGetLastError());
-  ctx->launches += 1;
+  ctx->launches += 2;
+  const int64_t tlo = ctx->sellLo.total, tup = ctx->sellUp.total;
+  DEC_TRY_STATUS(scatter_values<double>(ctx, ctx->sellLo, g, ctx->sGlo64.p + (int64_t)vs * tlo));
+  DEC_TRY_STATUS(scatter_values<double>(ctx, ctx->sellUp, g, ctx->sGup64.p + (int64_t)vs * tup));
+  DEC_TRY_STATUS(scatter_values<__nv_bfloat16>(ctx, ctx->sellLo, g, ctx->sGlo16.p + (int64_t)vs * tlo));
+  DEC_TRY_STATUS(scatter_values<__nv_bfloat16>(ctx, ctx->sellUp, g, ctx->sGup16.p + (int64_t)vs * tup));
   int flag = 0;
-  DEC_TRY(cudaMemcpyAsync(&flag, ctx->errflag.p, sizeof(int),
-                          cudaMemcpyDeviceToHost, s));
+  DEC_TRY(cudaMemcpyAsync(&flag, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   DEC_TRY(cudaStreamSynchronize(s));
   if (flag & 8)
     return ctx->fail(DEC_ERR_LIMIT, "an FSAI row has more than 32 lower-pattern entries");
