@@ -224,6 +224,40 @@ dec_status dec_time_kernel(dec_ctx* ctx, int32_t kernel, int32_t reps,
  * counting every kernel node of each replayed CUDA graph. */
 dec_status dec_get_launch_count(const dec_ctx* ctx, int64_t* count);
 
+/* ---- an entry point that allocates no device memory ---- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that must not let a library allocate device memory: code that runs inside
+ * a framework owning every device allocation through its own pool, under a
+ * fixed device-memory budget, or where a cudaMalloc would synchronise the
+ * device at a bad moment.  It computes the same three sums as dec_k_eff for
+ * one instance, from arrays the caller already holds, and needs no context:
+ *   q_in   = sum over edges (i,j) of w_e (T_i - T_j) signed by which end is a
+ *            Dirichlet node on x = 0 (outflow of those nodes),
+ *   q_out  = the same for Dirichlet nodes on x = 1 (inflow),
+ *   energy = sum over edges of w_e (T_i - T_j)^2.
+ *   device    CUDA device of the arrays; stream: cudaStream_t or NULL.
+ *   E         [n_edges*2] int32 device: edges (i, j).
+ *   w         [n_edges] f64 device: *1 of each edge (0 where cut).
+ *   T         [n_nodes] f64 device: temperatures (Dirichlet values included).
+ *   xyz       [n_nodes*3] f64 device; node_tag [n_nodes] uint8 device.
+ *   out3      [3] f64 host or device: q_in, q_out, energy.
+ * Its only scratch (per-block partial sums and an arrival counter) is a
+ * fixed 768 KiB array inside the library's device image, present on every
+ * GPU that loads the library until the process exits; n_edges may therefore
+ * not exceed 67,108,864 (DEC_ERR_LIMIT beyond).  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) once; make
+ * that first call before any stream capture.  Every call clears the counter
+ * and reuses the same array, so calls that overlap on the GPU (other
+ * streams, other host threads, on the same device) race: serialise them.
+ * The call returns after out3 is written.  No cudaMalloc or cudaFree is
+ * made.  Errors: DEC_ERR_ARG (NULL pointer, n_edges < 1, bad device),
+ * DEC_ERR_LIMIT, DEC_ERR_CUDA. */
+dec_status dec_k_eff_edges_noalloc(int device, void* stream, const int32_t* E,
+                                   int64_t n_edges, const double* w, const double* T,
+                                   const double* xyz, const uint8_t* node_tag,
+                                   double* out3);
+
 #ifdef __cplusplus
 }
 #endif

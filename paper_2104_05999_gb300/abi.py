@@ -57,6 +57,7 @@ SIGNATURES = {
     "dec_get_precond": [_P, _P],
     "dec_time_kernel": [_P, _I32, _I32, _I64, _P],
     "dec_get_launch_count": [_P, _P],
+    "dec_k_eff_edges_noalloc": [C.c_int, _P, _P, _I64, _P, _P, _P, _P, _P],
 }
 
 _lib = None
@@ -234,3 +235,16 @@ class Context:
                                              int(flush_bytes), C.byref(ms)))
         return ms.value
 
+
+def dec_k_eff_edges_noalloc(device, E, w, T, xyz, node_tag, stream=None):
+    """q_in, q_out, energy of one temperature field from device arrays,
+    through the entry point that allocates no device memory (see dec.h)."""
+    lib = load()
+    out = np.zeros(3)
+    st = lib.dec_k_eff_edges_noalloc(
+        int(device), stream, _ptr(E, np.int32), int(E.shape[0]),
+        _ptr(w, np.float64), _ptr(T, np.float64), _ptr(xyz, np.float64),
+        _ptr(node_tag, np.uint8), out.ctypes.data)
+    if st != DEC_OK:
+        raise DecError(st, "dec_k_eff_edges_noalloc failed")
+    return out
