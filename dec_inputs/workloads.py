@@ -44,7 +44,7 @@ class Workload:
     scales: np.ndarray | None  # f64[B] disc radius scales, None = [1]
     rtol: float                # relative residual the solve stops at
     precond: str               # "jacobi" | "fsai"
-    mode: str                  # "fp64" | "mixed"
+    mode: str                  # "fp64" | "mixed" | "batched"
 
     @property
     def n(self) -> int:
@@ -67,8 +67,8 @@ WORKLOADS = {
     "kuhn9":       (0, 9,   "kuhn",     0.0, 0,    None,          0,  1, 1e-12, "jacobi", "fp64"),
     "lognormal64": (1, 64,  "delaunay", 1.0, 0,    None,          0,  1, 1e-10, "fsai",   "fp64"),
     "cracked128":  (2, 128, "delaunay", 0.0, 2000, (0.02, 0.06),  0,  1, 1e-10, "fsai",   "mixed"),
-    "growth96":    (3, 96,  "delaunay", 0.0, 1500, (0.02, 0.05),  64, 1, 1e-10, "fsai",   "mixed"),
-    "hetero192":   (4, 192, "delaunay", 1.5, 5000, (0.02, 0.06),  0,  8, 1e-10, "fsai",   "mixed"),
+    "growth96":    (3, 96,  "delaunay", 0.0, 1500, (0.02, 0.05),  64, 1, 1e-10, "fsai",   "batched"),
+    "hetero192":   (4, 192, "delaunay", 1.5, 5000, (0.02, 0.06),  0,  8, 1e-10, "fsai",   "batched"),
 }
 
 

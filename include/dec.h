@@ -67,16 +67,31 @@ typedef enum {
 /* node tags (node_tag argument of dec_mesh_upload) */
 enum { DEC_NODE_FREE = 0, DEC_NODE_DIRICHLET = 1, DEC_NODE_NEUMANN = 2 };
 /* preconditioners (dec_laplacian_build) */
-enum { DEC_PRECOND_JACOBI = 0, DEC_PRECOND_FSAI = 1 };
+enum {
+  DEC_PRECOND_JACOBI = 0,       /* 1 / L_ii, per instance                     */
+  DEC_PRECOND_FSAI = 1,         /* FSAI factor per instance (value set)       */
+  DEC_PRECOND_FSAI_SHARED = 2   /* one FSAI factor, of the uncracked operator,
+                                   shared by every instance; prepares the
+                                   batched solve (DEC_MODE_MIXED_BATCHED)     */
+};
 /* solve modes (dec_solve) */
 enum {
   DEC_MODE_FP64 = 0,   /* PCG in FP64 (matrix, preconditioner, vectors)       */
-  DEC_MODE_MIXED = 1   /* PCG with FP32 vectors and L and a BF16 FSAI factor
+  DEC_MODE_MIXED = 1,  /* PCG with FP32 vectors and L and a BF16 FSAI factor
                           (FP32 Jacobi) inside FP64 defect correction: the
                           FP32 update is added to an FP64 solution x and the
                           FP32 residual replaced by r = b - L x in FP64 each
                           time it has dropped by 1e-2, keeping the search
-                          direction; convergence is decided in FP64        */
+                          direction; convergence is decided in FP64.  Runs
+                          as one persistent cooperative kernel per instance */
+  DEC_MODE_MIXED_PHASED = 2, /* the same solve as DEC_MODE_MIXED, run as one
+                                kernel per phase (CUDA graphs) instead    */
+  DEC_MODE_MIXED_BATCHED = 3  /* the mixed solve of all instances (crack
+                                states or Dirichlet sets, at most 64) in
+                                one persistent launch over a sparse matrix -
+                                multiple vector product, with per-instance
+                                convergence masks; needs
+                                DEC_PRECOND_FSAI_SHARED                    */
 };
 
 /* Local edge slots of a tet: slot s joins local vertices LOCAL[s] =
@@ -189,7 +204,9 @@ dec_status dec_get_hodge(dec_ctx* ctx, double* w, uint8_t* first_cut);
 
 /* CSR of L: rowptr [n_nodes+1] int32, col [nnz] int32, columns sorted,
  * diagonal included.  val [nnz] f64 and b [n_nodes] f64 of instance
- * `inst`.  Any pointer may be NULL.  Host or device buffers. */
+ * `inst` (after DEC_PRECOND_FSAI_SHARED, val is the uncracked operator
+ * shared by all instances, b is still per instance).  Any pointer may be
+ * NULL.  Host or device buffers. */
 dec_status dec_get_csr(dec_ctx* ctx, int32_t inst, int32_t* rowptr,
                        int32_t* col, double* val, double* b);
 

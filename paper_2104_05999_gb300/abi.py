@@ -31,8 +31,8 @@ STATUS_NAMES = {
     7: "DEC_ERR_STATE", 8: "DEC_ERR_LIMIT"}
 
 DEC_NODE_FREE, DEC_NODE_DIRICHLET, DEC_NODE_NEUMANN = 0, 1, 2
-DEC_PRECOND_JACOBI, DEC_PRECOND_FSAI = 0, 1
-DEC_MODE_FP64, DEC_MODE_MIXED = 0, 1
+DEC_PRECOND_JACOBI, DEC_PRECOND_FSAI, DEC_PRECOND_FSAI_SHARED = 0, 1, 2
+DEC_MODE_FP64, DEC_MODE_MIXED, DEC_MODE_MIXED_PHASED, DEC_MODE_MIXED_BATCHED = 0, 1, 2, 3
 DEC_KERNEL_SPMV_F64, DEC_KERNEL_SPMV_F32 = 0, 1
 DEC_KERNEL_FSAI_F64, DEC_KERNEL_FSAI_BF16 = 2, 3
 

@@ -200,7 +200,8 @@ dec_status dec_laplacian_build(dec_ctx* ctx, const double* T0, int32_t n_sets,
   ctx->err.clear();
   if (ctx->stage < 2) return ctx->fail(DEC_ERR_STATE, "laplacian_build: no Hodge star assembled");
   if (!T0 || n_sets < 1) return ctx->fail(DEC_ERR_ARG, "laplacian_build: bad T0 / n_sets");
-  if (precond != DEC_PRECOND_JACOBI && precond != DEC_PRECOND_FSAI)
+  if (precond != DEC_PRECOND_JACOBI && precond != DEC_PRECOND_FSAI &&
+      precond != DEC_PRECOND_FSAI_SHARED)
     return ctx->fail(DEC_ERR_ARG, "laplacian_build: unknown preconditioner");
   if (ctx->n_scales > 1 && n_sets > 1)
     return ctx->fail(DEC_ERR_ARG, "laplacian_build: crack states and several T0 sets at once");
@@ -211,13 +212,16 @@ dec_status dec_laplacian_build(dec_ctx* ctx, const double* T0, int32_t n_sets,
   ctx->n_sets = n_sets;
   ctx->precond = precond;
   ctx->B = std::max(ctx->n_scales, n_sets);
-  const int V = ctx->n_scales;  // value sets
+  const bool shared = precond == DEC_PRECOND_FSAI_SHARED;
+  if (shared && ctx->B > 64)
+    return ctx->fail(DEC_ERR_LIMIT, "laplacian_build: a batched solve takes at most 64 instances");
+  const int V = shared ? 1 : ctx->n_scales;  // value sets
   DEC_TRY(upload(ctx->T0, T0, (int64_t)n_sets * n, s));
   DEC_TRY(ctx->val64.ensure((size_t)V * nnz));
   DEC_TRY(ctx->sL64.ensure((size_t)V * ctx->sellL.total));
   DEC_TRY(ctx->sL32.ensure((size_t)V * ctx->sellL.total));
   DEC_TRY(ctx->b.ensure((size_t)ctx->B * n));
-  if (precond == DEC_PRECOND_FSAI) {
+  if (precond != DEC_PRECOND_JACOBI) {
     DEC_TRY(ctx->g64.ensure((size_t)V * nnz));
     DEC_TRY(ctx->sGlo64.ensure((size_t)V * ctx->sellLo.total));
     DEC_TRY(ctx->sGup64.ensure((size_t)V * ctx->sellUp.total));
@@ -227,8 +231,15 @@ dec_status dec_laplacian_build(dec_ctx* ctx, const double* T0, int32_t n_sets,
     DEC_TRY(ctx->dinv64.ensure((size_t)V * n));
     DEC_TRY(ctx->dinv32.ensure((size_t)V * n));
   }
-  for (int inst = 0; inst < ctx->B; ++inst) DEC_TRY_STATUS(dec::build_values(ctx, inst));
-  for (int vs = 0; vs < V; ++vs) DEC_TRY_STATUS(dec::build_precond(ctx, vs));
+  if (shared) {
+    // one FSAI factor of the uncracked operator, per-entry edge data, b[n][BS]
+    DEC_TRY_STATUS(dec::build_values_uncracked(ctx));
+    DEC_TRY_STATUS(dec::build_precond(ctx, 0));
+    DEC_TRY_STATUS(dec::batch_setup(ctx));
+  } else {
+    for (int inst = 0; inst < ctx->B; ++inst) DEC_TRY_STATUS(dec::build_values(ctx, inst));
+    for (int vs = 0; vs < V; ++vs) DEC_TRY_STATUS(dec::build_precond(ctx, vs));
+  }
   DEC_TRY(cudaStreamSynchronize(s));
   ctx->stage = 3;
   return DEC_OK;
@@ -241,8 +252,12 @@ dec_status dec_solve(dec_ctx* ctx, double rtol, int32_t max_iter, int32_t mode,
   if (ctx->stage < 3) return ctx->fail(DEC_ERR_STATE, "solve: no Laplacian built");
   if (!(rtol > 0.0) || !std::isfinite(rtol) || max_iter < 1)
     return ctx->fail(DEC_ERR_ARG, "solve: rtol must be > 0 and max_iter >= 1");
-  if (mode != DEC_MODE_FP64 && mode != DEC_MODE_MIXED)
+  if (mode != DEC_MODE_FP64 && mode != DEC_MODE_MIXED && mode != DEC_MODE_MIXED_PHASED &&
+      mode != DEC_MODE_MIXED_BATCHED)
     return ctx->fail(DEC_ERR_ARG, "solve: unknown mode");
+  if ((mode == DEC_MODE_MIXED_BATCHED) != (ctx->precond == DEC_PRECOND_FSAI_SHARED))
+    return ctx->fail(DEC_ERR_STATE,
+                     "solve: DEC_MODE_MIXED_BATCHED goes with DEC_PRECOND_FSAI_SHARED only");
   DEC_TRY_STATUS(set_device(ctx));
   cudaStream_t s = ctx->stream;
   const int64_t n = ctx->n;
@@ -260,11 +275,17 @@ dec_status dec_solve(dec_ctx* ctx, double rtol, int32_t max_iter, int32_t mode,
   ctx->iters_host.assign(ctx->B, 0);
   ctx->relres_host.assign(ctx->B, 0.0);
   dec_status worst = DEC_OK;
-  for (int inst = 0; inst < ctx->B; ++inst) {
-    dec_status st = dec::solve_instance(ctx, inst, rtol, max_iter, mode,
-                                        &ctx->iters_host[inst], &ctx->relres_host[inst]);
-    if (st == DEC_ERR_CUDA) return st;
-    if (st != DEC_OK && worst == DEC_OK) worst = st;
+  if (mode == DEC_MODE_MIXED_BATCHED) {
+    worst = dec::solve_batched(ctx, rtol, max_iter, ctx->iters_host.data(),
+                               ctx->relres_host.data());
+    if (worst == DEC_ERR_CUDA || worst == DEC_ERR_LIMIT) return worst;
+  } else {
+    for (int inst = 0; inst < ctx->B; ++inst) {
+      dec_status st = dec::solve_instance(ctx, inst, rtol, max_iter, mode,
+                                          &ctx->iters_host[inst], &ctx->relres_host[inst]);
+      if (st == DEC_ERR_CUDA) return st;
+      if (st != DEC_OK && worst == DEC_OK) worst = st;
+    }
   }
   std::string keep = ctx->err;
   if (T_out) {
@@ -339,7 +360,7 @@ dec_status dec_get_csr(dec_ctx* ctx, int32_t inst, int32_t* rowptr, int32_t* col
   cudaStream_t s = ctx->stream;
   DEC_TRY(download(rowptr, (const int32_t*)ctx->rowptr.p, ctx->n + 1, s));
   DEC_TRY(download(col, (const int32_t*)ctx->col.p, ctx->nnz, s));
-  const int vs = ctx->n_scales > 1 ? inst : 0;
+  const int vs = (ctx->n_scales > 1 && ctx->precond != DEC_PRECOND_FSAI_SHARED) ? inst : 0;
   if (val) DEC_TRY(download(val, (const double*)ctx->val64.p + (int64_t)vs * ctx->nnz, ctx->nnz, s));
   if (b) DEC_TRY(download(b, (const double*)ctx->b.p + (int64_t)inst * ctx->n, ctx->n, s));
   DEC_TRY(cudaStreamSynchronize(s));
@@ -378,7 +399,7 @@ dec_status dec_time_kernel(dec_ctx* ctx, int32_t kernel, int32_t reps,
   if (ctx->stage < 3) return ctx->fail(DEC_ERR_STATE, "time_kernel: no Laplacian built");
   if (reps < 1 || flush_bytes < 0 || !avg_ms) return ctx->fail(DEC_ERR_ARG, "time_kernel: bad arguments");
   if ((kernel == DEC_KERNEL_FSAI_F64 || kernel == DEC_KERNEL_FSAI_BF16) &&
-      ctx->precond != DEC_PRECOND_FSAI)
+      ctx->precond == DEC_PRECOND_JACOBI)
     return ctx->fail(DEC_ERR_STATE, "time_kernel: no FSAI factor built");
   DEC_TRY_STATUS(set_device(ctx));
   return dec::time_kernel(ctx, kernel, reps, (size_t)flush_bytes, avg_ms);

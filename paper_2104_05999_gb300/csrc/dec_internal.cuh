@@ -135,6 +135,13 @@ struct dec_ctx {
   dec::DevBuf<float> sL32;
   dec::DevBuf<__nv_bfloat16> sGlo16, sGup16;
   dec::DevBuf<int32_t> big_rows;   // FSAI rows for the warp-per-row kernel
+  dec::DevBuf<int64_t> coop;       // persistent solve: barrier, status, result
+  // batched solve: shared per-entry data, factor copy, [n][BS] vectors
+  dec::DevBuf<float> bw32;
+  dec::DevBuf<double> bw64, bb, bx64, br64, bpartial;
+  dec::DevBuf<uint8_t> bfc;
+  dec::DevBuf<__nv_bfloat16> bg16;
+  dec::DevBuf<float> bx, br, bz, bp, bq, bt;
   std::vector<int> iters_host;
   std::vector<double> relres_host;
 
@@ -155,7 +162,10 @@ struct dec_ctx {
     cg.release(); out3.release(); flush.release();
     sellL.release(); sellLo.release(); sellUp.release(); sL64.release();
     sGlo64.release(); sGup64.release(); sL32.release(); sGlo16.release();
-    sGup16.release(); big_rows.release();
+    sGup16.release(); big_rows.release(); coop.release(); bw32.release();
+    bw64.release(); bb.release(); bx64.release(); br64.release(); bpartial.release();
+    bfc.release(); bg16.release(); bx.release(); br.release(); bz.release();
+    bp.release(); bq.release(); bt.release();
   }
 
   dec_status fail(dec_status s, const std::string& what) {
@@ -194,13 +204,34 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Sum `v` over the block into thread 0 (fixed order: deterministic).
+// Sum `v` over the block into thread 0, in a fixed order (deterministic).
+// GB300's FP64 pipe is narrow and a warp-wide FP64 shuffle sum costs 5 FP64
+// instructions per warp, so only warp 0 adds in FP64: the block's values go
+// through shared memory (sh: NT doubles) and warp 0 sums NT/32 of them per
+// lane before one shuffle sum.
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
-  if (lane == 0) sh[wid] = v;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NT / 32; ++j) t += sh[lane + 32 * j];
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// The same for FP32 contributions: warps add in FP32, warp 0 adds the warp
+// sums in FP64.  sh needs 32 doubles.
+template <int NT>
+__device__ __forceinline__ double block_sum_f(float v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = (double)v;
   __syncthreads();
   double t = 0.0;
   if (wid == 0) {
@@ -208,6 +239,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     t = warp_sum(t);
   }
   return t;
+}
+
+// Sum of `count` doubles at p (stride 1) by warp 0, in a fixed order; the
+// result is valid in lane 0 of warp 0.
+__device__ __forceinline__ double warp0_sum_array(const double* p, int count) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < count; i += 32) a += __ldcg(p + i);
+  return warp_sum(a);
 }
 
 // Deterministic grid reduction of NV doubles per thread.  Every block
@@ -220,7 +259,8 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV],
                                             double (&tot)[NV],
                                             double* partial,
                                             unsigned* ticket) {
-  __shared__ double sh[32];
+  __shared__ double sh[NT];
+  __shared__ double res[NV];
   __shared__ bool last;
 #pragma unroll
   for (int s = 0; s < NV; ++s) {
@@ -236,18 +276,16 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV],
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  if (threadIdx.x < 32) {
 #pragma unroll
-  for (int s = 0; s < NV; ++s) {
-    double a = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += NT)
-      a += __ldcg(&partial[s * gridDim.x + i]);
-    double t = block_sum<NT>(a, sh);
-    __syncthreads();
-    if (threadIdx.x == 0) sh[0] = t;
-    __syncthreads();
-    tot[s] = sh[0];
-    __syncthreads();
+    for (int s = 0; s < NV; ++s) {
+      const double t = warp0_sum_array(partial + s * gridDim.x, (int)gridDim.x);
+      if (threadIdx.x == 0) res[s] = t;
+    }
   }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < NV; ++s) tot[s] = res[s];
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
 }
@@ -277,11 +315,17 @@ dec_status validate_k(dec_ctx* ctx);
 // system
 dec_status build_values(dec_ctx* ctx, int inst);
 dec_status build_precond(dec_ctx* ctx, int vs);
+dec_status build_values_uncracked(dec_ctx* ctx);
 // solve
 dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
                           int mode, int* iters, double* relres);
 dec_status k_eff_instance(dec_ctx* ctx, int inst, double* out3);
 dec_status form_T(dec_ctx* ctx, int inst, double* T);
+dec_status solve_mixed_persistent(dec_ctx* ctx, int inst, double rtol, int max_iter,
+                                  int* iters_out, double* relres_out);
+dec_status batch_setup(dec_ctx* ctx);
+dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
+                         double* relres);
 dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
                        double* avg_ms);
 }  // namespace dec

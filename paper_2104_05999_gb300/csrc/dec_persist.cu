@@ -1,0 +1,367 @@
+// dec_persist.cu - the mixed-precision PCG of one instance as a single
+// persistent kernel (cooperative launch: every block is resident).
+//
+// The solve is the one of the mixed mode in dec_solver.cu: CG with FP32
+// vectors and L, a BF16 FSAI factor (or FP32 Jacobi), and FP64 defect
+// correction by reliable updates (x64 += x32, r = b - L x64 in FP64 each time
+// the FP32 residual has dropped by 1e-2; convergence decided in FP64).  The
+// phases of an iteration are separated by a grid barrier instead of kernel
+// boundaries, and every reduction ends with all blocks summing the block
+// partials in the same order, so each block holds the same alpha, beta and
+// residuals and takes the same branch without a host round trip.
+//
+// The barrier spins on a generation counter with a bounded number of polls;
+// when the bound is hit the kernel records DEC_ERR_TIMEOUT and every block
+// leaves at its next barrier.
+#include "dec_kern.cuh"
+
+#include <algorithm>
+
+namespace dec {
+
+constexpr long kSpinLimit = 1L << 24;   // polls of 32-256 ns: a few seconds
+// One block of 1024 threads per SM: fewer blocks make the grid barrier and
+// the all-blocks partial sums cheaper (they cost per block, not per thread).
+constexpr int kPBlock = 1024;
+
+struct PersistArgs {
+  int64_t n;
+  SellArg<float> A32;
+  SellArg<double> A64;
+  SellArg<__nv_bfloat16> Glo, Gup;
+  const float* dinv;          // Jacobi, or nullptr for FSAI
+  const double* b;
+  double *x64, *r64;
+  float *x, *r, *z, *p, *q, *t;
+  double* partial;            // [4][gridDim.x]
+  unsigned* bar;              // [0] arrivals, [1] generation
+  int* status;                // [0] error, [1] iterations, [2] outcome
+  double* result;             // [0] final rr (FP64), [1] |b|^2
+  double rtol2, seg2;
+  int max_iter;
+};
+
+// Grid barrier with a bounded spin.  Returns false once any block has
+// timed out (then every block leaves).
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long polls = 0;
+      unsigned ns = 32;
+      while (*gen == g) {
+        if (++polls > kSpinLimit || *(volatile int*)err) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)err == 0;
+}
+
+// Sum of NV (<= 2) per-thread values over the grid, identical in every
+// block.  Consecutive calls alternate between two partial buffers: a block
+// may write the partials of one sum while a slower block still reads those
+// of the previous one, but never those of the one before (a barrier lies in
+// between).  FP32 contributions (T = float) are added in FP32 inside each
+// warp; everything above the warp level is FP64 and done by warp 0 alone
+// (GB300's FP64 pipe is narrow, so FP64 work by every warp would dominate).
+template <int NV, typename T>
+__device__ __forceinline__ bool grid_sum(const T (&v)[NV], double (&tot)[NV],
+                                         double* partial, int& parity, unsigned* bar,
+                                         int* err) {
+  __shared__ double sh[kPBlock];
+  __shared__ double bc[2];
+  double* part = partial + (size_t)parity * 2 * gridDim.x;
+  parity ^= 1;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s;
+    if constexpr (sizeof(T) == 4) s = block_sum_f<kPBlock>(v[k], sh);
+    else s = block_sum<kPBlock>(v[k], sh);
+    if (threadIdx.x == 0) part[k * gridDim.x + blockIdx.x] = s;
+  }
+  if (!grid_sync(bar, err)) return false;
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const double t = warp0_sum_array(part + k * gridDim.x, (int)gridDim.x);
+      if (threadIdx.x == 0) bc[k] = t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = bc[k];
+  __syncthreads();
+  return true;
+}
+
+template <bool JACOBI>
+__global__ void __launch_bounds__(kPBlock, 1)
+pcg_mixed_persistent(PersistArgs a) {
+  const int64_t n = a.n;
+  const int64_t gtid = blockIdx.x * (int64_t)kPBlock + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * kPBlock;
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = gtid >> 5, nwarps = gstride >> 5;
+  int* err = a.status;
+  // scalars derived from reductions: thread 0 computes, the block reads
+  // (one FP64 division per block instead of one per thread)
+  __shared__ float s_scal;
+  __shared__ int s_flag;
+  auto finish = [&](int outcome, int iters, double rr, double bb) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.status[1] = iters;
+      a.status[2] = outcome;
+      a.result[0] = rr;
+      a.result[1] = bb;
+    }
+  };
+
+  // ---- start: x64 = 0, r64 = b, r = (float) b, x = p = 0
+  int parity = 0;
+  double v1[1], t1[1];
+  {
+    double bb = 0.0;
+    for (int64_t i = gtid; i < n; i += gstride) {
+      const double bi = a.b[i];
+      a.x64[i] = 0.0;
+      a.r64[i] = bi;
+      a.r[i] = (float)bi;
+      a.x[i] = 0.0f;
+      a.p[i] = 0.0f;
+      bb += bi * bi;
+    }
+    v1[0] = bb;
+  }
+  if (!grid_sum<1>(v1, t1, a.partial, parity, a.bar, err)) return;
+  const double bnorm2 = t1[0];
+  if (bnorm2 == 0.0) { finish(0, 0, 0.0, 0.0); return; }
+  double rr64 = bnorm2, best = bnorm2, rz = 0.0;
+  double tol2 = a.seg2 * rr64;
+  int iters = 0, stall = 0, restart = 1;
+
+  for (;;) {
+    // ---- (re)start of a segment: z = M r, beta, p = z + beta p
+    {
+      float v[1] = {0.0f};
+      double t[1];
+      if (JACOBI) {
+        float acc = 0.0f;
+        for (int64_t i = gtid; i < n; i += gstride) {
+          const float zi = a.dinv[i] * a.r[i];
+          a.z[i] = zi;
+          acc = fmaf(a.r[i], zi, acc);
+        }
+        v[0] = acc;
+      } else {
+        for (int64_t s = gwarp; s < a.Glo.nslices; s += nwarps) {
+          const int32_t row = __ldg(a.Glo.perm + 32 * s + lane);
+          const float acc = sell_row(a.Glo, s, lane, a.r);
+          if (row >= 0) a.t[row] = acc;
+        }
+        if (!grid_sync(a.bar, err)) return;
+        float acc2 = 0.0f;
+        for (int64_t s = gwarp; s < a.Gup.nslices; s += nwarps) {
+          const int32_t row = __ldg(a.Gup.perm + 32 * s + lane);
+          const float acc = sell_row(a.Gup, s, lane, a.t);
+          if (row >= 0) {
+            a.z[row] = acc;
+            acc2 = fmaf(a.r[row], acc, acc2);
+          }
+        }
+        v[0] = acc2;
+      }
+      if (!grid_sum<1>(v, t, a.partial, parity, a.bar, err)) return;
+      if (threadIdx.x == 0) s_scal = restart ? 0.0f : (float)(t[0] / rz);
+      __syncthreads();
+      rz = t[0];
+      const float fb = s_scal;
+      for (int64_t i = gtid; i < n; i += gstride) a.p[i] = fmaf(fb, a.p[i], a.z[i]);
+      if (!grid_sync(a.bar, err)) return;
+    }
+    // ---- FP32 iterations until the residual has dropped by seg2
+    int breakdown = 0;
+    for (;;) {
+      // q = A p, p.q
+      float v[2] = {0.0f, 0.0f};
+      double t[2];
+      float vq[1];
+      double tq[1];
+      {
+        float acc2 = 0.0f;
+        for (int64_t s = gwarp; s < a.A32.nslices; s += nwarps) {
+          const int32_t row = __ldg(a.A32.perm + 32 * s + lane);
+          const float acc = sell_row(a.A32, s, lane, a.p);
+          if (row >= 0) {
+            a.q[row] = acc;
+            acc2 = fmaf(a.p[row], acc, acc2);
+          }
+        }
+        vq[0] = acc2;
+      }
+      if (!grid_sum<1>(vq, tq, a.partial, parity, a.bar, err)) return;
+      if (threadIdx.x == 0) {
+        const double pq = tq[0];
+        s_flag = (!(pq > 0.0) || !isfinite(pq)) ? 1 : 0;
+        s_scal = s_flag ? 0.0f : (float)(rz / pq);
+      }
+      __syncthreads();
+      if (s_flag) { breakdown = 1; break; }
+      const float alpha = s_scal;
+      // x += alpha p, r -= alpha q, r.r (and Jacobi z, r.z)
+      {
+        float rr = 0.0f, rzj = 0.0f;
+        for (int64_t i = gtid; i < n; i += gstride) {
+          const float ri = fmaf(-alpha, a.q[i], a.r[i]);
+          a.x[i] = fmaf(alpha, a.p[i], a.x[i]);
+          a.r[i] = ri;
+          rr = fmaf(ri, ri, rr);
+          if (JACOBI) {
+            const float zi = a.dinv[i] * ri;
+            a.z[i] = zi;
+            rzj = fmaf(ri, zi, rzj);
+          }
+        }
+        v[0] = rr;
+        v[1] = rzj;
+      }
+      if (!grid_sum<2>(v, t, a.partial, parity, a.bar, err)) return;
+      ++iters;
+      const double rr = t[0];
+      if (rr <= tol2 || iters >= a.max_iter || !isfinite(rr)) break;
+      double rz_new;
+      if (JACOBI) {
+        rz_new = t[1];
+      } else {
+        for (int64_t s = gwarp; s < a.Glo.nslices; s += nwarps) {
+          const int32_t row = __ldg(a.Glo.perm + 32 * s + lane);
+          const float acc = sell_row(a.Glo, s, lane, a.r);
+          if (row >= 0) a.t[row] = acc;
+        }
+        if (!grid_sync(a.bar, err)) return;
+        float acc2 = 0.0f;
+        for (int64_t s = gwarp; s < a.Gup.nslices; s += nwarps) {
+          const int32_t row = __ldg(a.Gup.perm + 32 * s + lane);
+          const float acc = sell_row(a.Gup, s, lane, a.t);
+          if (row >= 0) {
+            a.z[row] = acc;
+            acc2 = fmaf(a.r[row], acc, acc2);
+          }
+        }
+        float vz[1] = {acc2};
+        double tz[1];
+        if (!grid_sum<1>(vz, tz, a.partial, parity, a.bar, err)) return;
+        rz_new = tz[0];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_scal = (float)(rz_new / rz);
+      __syncthreads();
+      const float beta = s_scal;
+      rz = rz_new;
+      for (int64_t i = gtid; i < n; i += gstride) a.p[i] = fmaf(beta, a.p[i], a.z[i]);
+      if (!grid_sync(a.bar, err)) return;
+    }
+    // ---- reliable update: x64 += x, x = 0; r64 = b - L x64; r = (float) r64
+    for (int64_t i = gtid; i < n; i += gstride) {
+      a.x64[i] += (double)a.x[i];
+      a.x[i] = 0.0f;
+    }
+    if (!grid_sync(a.bar, err)) return;
+    {
+      double rr = 0.0;
+      for (int64_t s = gwarp; s < a.A64.nslices; s += nwarps) {
+        const int32_t row = __ldg(a.A64.perm + 32 * s + lane);
+        const double acc = sell_row(a.A64, s, lane, a.x64);
+        if (row >= 0) {
+          const double ri = a.b[row] - acc;
+          a.r64[row] = ri;
+          a.r[row] = (float)ri;
+          rr = fma(ri, ri, rr);
+        }
+      }
+      v1[0] = rr;
+    }
+    if (!grid_sum<1>(v1, t1, a.partial, parity, a.bar, err)) return;
+    rr64 = t1[0];
+    if (rr64 <= a.rtol2 * bnorm2) { finish(0, iters, rr64, bnorm2); return; }
+    if (iters >= a.max_iter) { finish(1, iters, rr64, bnorm2); return; }
+    if (rr64 < 0.5 * best) { best = rr64; stall = 0; }
+    else if (++stall >= 4) { finish(2, iters, rr64, bnorm2); return; }
+    restart = (breakdown || stall > 0) ? 1 : 0;
+    tol2 = a.seg2 * rr64;
+  }
+}
+
+// One mixed-precision solve of instance `inst` with the persistent kernel.
+// Returns DEC_ERR_LIMIT when a cooperative launch is not possible (the
+// caller then uses the kernel-per-phase path).
+dec_status solve_mixed_persistent(dec_ctx* ctx, int inst, double rtol, int max_iter,
+                                  int* iters_out, double* relres_out) {
+  const int64_t n = ctx->n;
+  const int vs = ctx->n_scales > 1 ? inst : 0;
+  cudaStream_t s = ctx->stream;
+  const bool fsai = ctx->precond == DEC_PRECOND_FSAI;
+  int dev_coop = 0;
+  DEC_TRY(cudaDeviceGetAttribute(&dev_coop, cudaDevAttrCooperativeLaunch, ctx->device));
+  if (!dev_coop) return DEC_ERR_LIMIT;
+  auto kern = fsai ? pcg_mixed_persistent<false> : pcg_mixed_persistent<true>;
+  int per_sm = 0;
+  DEC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPBlock, 0));
+  if (per_sm < 1) return DEC_ERR_LIMIT;
+  const int grid = ctx->num_sms;   // one block per SM (per_sm >= 1 checked)
+  DEC_TRY(ctx->partial.ensure((size_t)kRedSlots * std::max(grid, ctx->reduce_grid)));
+  DEC_TRY(ctx->coop.ensure(16));
+  unsigned* bar = reinterpret_cast<unsigned*>(ctx->coop.p);
+  int* status = reinterpret_cast<int*>(ctx->coop.p + 2);
+  double* result = reinterpret_cast<double*>(ctx->coop.p + 8);
+  DEC_TRY(cudaMemsetAsync(ctx->coop.p, 0, 16 * sizeof(int64_t), s));
+  PersistArgs a{};
+  a.n = n;
+  a.A32 = sell_arg(ctx->sellL, ctx->sL32.p + (int64_t)vs * ctx->sellL.total);
+  a.A64 = sell_arg(ctx->sellL, ctx->sL64.p + (int64_t)vs * ctx->sellL.total);
+  a.Glo = sell_arg(ctx->sellLo, fsai ? ctx->sGlo16.p + (int64_t)vs * ctx->sellLo.total : nullptr);
+  a.Gup = sell_arg(ctx->sellUp, fsai ? ctx->sGup16.p + (int64_t)vs * ctx->sellUp.total : nullptr);
+  a.dinv = fsai ? nullptr : ctx->dinv32.p + (int64_t)vs * n;
+  a.b = ctx->b.p + (int64_t)inst * n;
+  a.x64 = ctx->u.p + (int64_t)inst * n;
+  a.r64 = ctx->r64.p;
+  a.x = ctx->x32.p; a.r = ctx->r32.p; a.z = ctx->z32.p; a.p = ctx->p32.p;
+  a.q = ctx->q32.p; a.t = ctx->t32.p;
+  a.partial = ctx->partial.p;
+  a.bar = bar;
+  a.status = status;
+  a.result = result;
+  a.rtol2 = rtol * rtol;
+  a.seg2 = 1e-4;
+  a.max_iter = max_iter;
+  void* args[] = {&a};
+  DEC_TRY(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kPBlock), args, 0, s));
+  ctx->launches += 1;
+  int hs[3];
+  double hr[2];
+  DEC_TRY(cudaMemcpyAsync(hs, status, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  DEC_TRY(cudaMemcpyAsync(hr, result, sizeof(hr), cudaMemcpyDeviceToHost, s));
+  DEC_TRY(cudaStreamSynchronize(s));
+  *iters_out = hs[1];
+  *relres_out = hr[1] > 0.0 ? std::sqrt(hr[0] / hr[1]) : 0.0;
+  if (hs[0]) return ctx->fail(DEC_ERR_TIMEOUT, "persistent solve: a grid barrier timed out");
+  if (hs[2] == 1) return ctx->fail(DEC_NOT_CONVERGED, "max_iter reached");
+  if (hs[2] == 2) return ctx->fail(DEC_NOT_CONVERGED, "residual replacement stalled");
+  return DEC_OK;
+}
+
+}  // namespace dec

@@ -15,68 +15,12 @@
 //               FP32 Jacobi), whose residual is replaced by the FP64 residual
 //               b - L x of an FP64 solution x every time it has dropped by
 //               1e-2 (defect correction that keeps the search direction).
-#include "dec_internal.cuh"
+#include "dec_kern.cuh"
 
 #include <algorithm>
 #include <cmath>
 
 namespace dec {
-
-__device__ __forceinline__ double to_d(double v) { return v; }
-__device__ __forceinline__ double to_d(float v) { return (double)v; }
-
-__device__ __forceinline__ double fma_(double a, double x, double acc) { return fma(a, x, acc); }
-__device__ __forceinline__ float fma_(float a, float x, float acc) { return fmaf(a, x, acc); }
-__device__ __forceinline__ float fma_(__nv_bfloat16 a, float x, float acc) {
-  return fmaf(__bfloat162float(a), x, acc);
-}
-
-// Matrix in SELL form, as kernel arguments.
-template <typename T>
-struct SellArg {
-  const int32_t* perm;
-  const int32_t* sptr;
-  const int32_t* col;
-  const T* val;
-  int64_t nslices;
-};
-
-template <typename T>
-static SellArg<T> sell_arg(const SellLayout& L, const T* val) {
-  return SellArg<T>{L.perm.p, L.sptr.p, L.col.p, val, L.nslices};
-}
-
-// Row sum of the lane's row in slice s: sum_j val * x[col].  Entries are
-// taken 8 at a time: 8 column and 8 value loads, then 8 independent gathers,
-// then the FMAs, so each warp keeps many loads in flight (the width w is
-// uniform across the warp, so the guards never diverge).
-template <typename MT, typename VT>
-__device__ __forceinline__ VT sell_row(const SellArg<MT>& A, int64_t s, int lane,
-                                       const VT* __restrict__ x) {
-  constexpr int U = 8;
-  const int32_t base = __ldg(A.sptr + s);
-  const int32_t w = (__ldg(A.sptr + s + 1) - base) >> 5;
-  const int32_t* __restrict__ cp = A.col + base + lane;
-  const MT* __restrict__ vp = A.val + base + lane;
-  VT acc = VT(0);
-  for (int32_t j = 0; j < w; j += U) {
-    int32_t c[U];
-    MT a[U];
-    VT xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool ok = j + u < w;
-      c[u] = ok ? __ldg(cp + 32 * (j + u)) : 0;
-      a[u] = ok ? vp[32 * (j + u)] : MT(0);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = j + u < w ? __ldg(x + c[u]) : VT(0);
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (j + u < w) acc = fma_(a[u], xv[u], acc);   // uniform: no idle FMAs
-  }
-  return acc;
-}
 
 // ------------------------------------------------------------ kernels
 // Element-wise kernels run grid_vec blocks (grid-stride over rows); SELL
@@ -518,7 +462,12 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
       DEC_TRY(cudaGetLastError());
     }
     DEC_TRY(cudaMemcpyAsync(u, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else if (mode == DEC_MODE_MIXED &&
+             (st = solve_mixed_persistent(ctx, inst, rtol, max_iter, iters_out, relres_out)) !=
+                 DEC_ERR_LIMIT) {
+    return st;   // the whole mixed solve ran as one cooperative kernel
   } else {
+    st = DEC_OK;
     // Mixed: one FP32 PCG whose residual is replaced, every time it has
     // dropped by kSegment since the last replacement, by the FP64 residual
     // b - L x of the FP64 solution x += (FP32 accumulated update) ("reliable

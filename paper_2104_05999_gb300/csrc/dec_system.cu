@@ -295,6 +295,22 @@ dec_status build_values(dec_ctx* ctx, int inst) {
   return DEC_OK;
 }
 
+// Value set 0 = the uncracked operator (no edge cut in any state) with the
+// first Dirichlet set: the matrix whose FSAI factor a batched solve shares.
+dec_status build_values_uncracked(dec_ctx* ctx) {
+  const int64_t n = ctx->n;
+  laplacian_values_kernel<<<grid_rows(ctx, n, 256), 256, 0, ctx->stream>>>(
+      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->w.p,
+      ctx->first_cut.p, -1, ctx->T0.p, ctx->val64.p, ctx->b.p);
+  DEC_TRY(cudaGetLastError());
+  ctx->launches += 1;
+  const int64_t tot = ctx->sellL.total;
+  DEC_TRY_STATUS(scatter_values<double>(ctx, ctx->sellL, ctx->val64.p, ctx->sL64.p));
+  DEC_TRY_STATUS(scatter_values<float>(ctx, ctx->sellL, ctx->val64.p, ctx->sL32.p));
+  (void)tot;
+  return DEC_OK;
+}
+
 dec_status build_precond(dec_ctx* ctx, int vs) {
   const int64_t n = ctx->n, nnz = ctx->nnz;
   const double* val = ctx->val64.p + (int64_t)vs * nnz;

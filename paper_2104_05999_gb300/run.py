@@ -28,12 +28,17 @@ def run_path(ctx: abi.Context, xyz, tets, tags, T0, k=None, discs=None,
     and (optionally) the temperature field of every instance."""
     ctx.dec_mesh_upload(xyz, tets, tags)
     ctx.dec_hodge_assemble(k, discs, scales)
-    pc = abi.DEC_PRECOND_FSAI if precond == "fsai" else abi.DEC_PRECOND_JACOBI
+    pc = {"fsai": abi.DEC_PRECOND_FSAI, "jacobi": abi.DEC_PRECOND_JACOBI,
+          "fsai_shared": abi.DEC_PRECOND_FSAI_SHARED}[precond]
+    if mode == "batched":
+        pc = abi.DEC_PRECOND_FSAI_SHARED
     ctx.dec_laplacian_build(T0, pc)
     B = ctx.sizes()[4]
     n = len(xyz)
     T = np.zeros((B, n)) if want_T else None
-    md = abi.DEC_MODE_MIXED if mode == "mixed" else abi.DEC_MODE_FP64
+    md = {"fp64": abi.DEC_MODE_FP64, "mixed": abi.DEC_MODE_MIXED,
+          "mixed_phased": abi.DEC_MODE_MIXED_PHASED,
+          "batched": abi.DEC_MODE_MIXED_BATCHED}[mode]
     st, iters, relres = ctx.dec_solve(rtol, max_iter, md, T,
                                       raise_on_error=raise_on_error)
     q_in, q_out, energy = ctx.dec_k_eff()

@@ -124,8 +124,9 @@ def test_kuhn9_jacobi_fp64_is_exact(abi, ctx):
 
 
 @pytest.mark.parametrize("precond,mode", [("jacobi", "fp64"), ("fsai", "fp64"),
-                                          ("fsai", "mixed"),
-                                          ("jacobi", "mixed")])
+                                          ("fsai", "mixed"), ("jacobi", "mixed"),
+                                          ("fsai", "mixed_phased"),
+                                          ("jacobi", "mixed_phased")])
 @pytest.mark.parametrize("N", [9, 16])
 def test_lognormal_solve_matches_oracle(abi, ctx, precond, mode, N):
     wl = make_workload("lognormal64", N=N)
@@ -281,3 +282,63 @@ def test_device_resident_inputs(abi, ctx):
     host = _run(abi, ctx, wl, "fsai", "fp64", 1e-10)
     assert np.array_equal(res.T, host.T)        # deterministic reductions
     assert res.q_in[0] == host.q_in[0]
+
+
+# ------------------------------------------------------------ batched solve
+
+def test_batched_crack_states_match_oracle(abi, ctx):
+    """All crack states of a growing disc population in one batched launch
+    (shared FSAI factor of the uncracked operator, per-instance masks)."""
+    wl = make_workload("growth96", N=10, n_discs=8, n_scales=6)
+    ref = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k,
+                       discs=wl.discs, scales=wl.scales, precond="fsai",
+                       rtol=1e-13)
+    res = _run(abi, ctx, wl, "fsai_shared", "batched", 1e-10, discs=wl.discs,
+               scales=wl.scales)
+    assert (res.relres <= 1e-10).all() and (res.iters > 0).all()
+    _, fc = ctx.dec_get_hodge()
+    E, t2e = ctx.dec_get_edges()
+    _crack_band(wl, E, t2e, wl.discs, wl.scales, fc.astype(np.int64),
+                ref["first_cut"])
+    for s in range(len(wl.scales)):
+        Tr = ref["T"][s]
+        assert np.linalg.norm(res.T[s] - Tr) / np.linalg.norm(Tr) <= T_RTOL
+    np.testing.assert_allclose(res.q_in, ref["q_in"], rtol=K_RTOL)
+    # right-hand sides of the batched set-up equal the oracle's per state
+    for s in (0, len(wl.scales) - 1):
+        _, _, _, b = ctx.dec_get_csr(s)
+        np.testing.assert_allclose(b, ref["b"][s], rtol=0,
+                                   atol=W_RTOL * np.abs(ref["b"][s]).max())
+
+
+def test_batched_dirichlet_sets_match_oracle(abi, ctx):
+    wl = make_workload("hetero192", N=9, n_sets=5)
+    ref = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k,
+                       discs=wl.discs, precond="fsai", rtol=1e-13)
+    res = _run(abi, ctx, wl, "fsai_shared", "batched", 1e-10, discs=wl.discs)
+    for s in range(5):
+        Tr = ref["T"][s]
+        assert np.linalg.norm(res.T[s] - Tr) / np.linalg.norm(Tr) <= T_RTOL
+        assert abs(res.energy[s] - ref["energy"][s]) <= K_RTOL * ref["energy"][s]
+
+
+def test_batched_64_states_widest_stride(abi, ctx):
+    # 64 instances: one row per 64 threads, the largest instance stride
+    wl = make_workload("growth96", N=8, n_discs=5, n_scales=64)
+    ref = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k,
+                       discs=wl.discs, scales=wl.scales, precond="jacobi",
+                       rtol=1e-13)
+    res = _run(abi, ctx, wl, "fsai_shared", "batched", 1e-10, discs=wl.discs,
+               scales=wl.scales)
+    np.testing.assert_allclose(res.q_in, ref["q_in"], rtol=K_RTOL)
+    assert (np.diff(res.q_in) <= 1e-9).all()
+
+
+def test_batched_mode_needs_shared_factor(abi, ctx):
+    wl = make_workload("growth96", N=6, n_discs=3, n_scales=3)
+    ctx.dec_mesh_upload(wl.xyz, wl.tets, wl.tags)
+    ctx.dec_hodge_assemble(wl.k, wl.discs, wl.scales)
+    ctx.dec_laplacian_build(wl.T0, abi.DEC_PRECOND_FSAI)
+    st, _, _ = ctx.dec_solve(1e-10, 1000, abi.DEC_MODE_MIXED_BATCHED,
+                             raise_on_error=False)
+    assert st == abi.DEC_ERR_STATE
