@@ -44,6 +44,7 @@ struct BatchArgs {
   const uint8_t* fc;                      // [nnz] first crack state (255: never)
   int states;                             // 1: instance b is crack state b; 0: all state 0
   const __nv_bfloat16* g;                 // [nnz] shared FSAI factor, CSR layout
+  const __nv_bfloat16* gb;                // [nnz][BS] per-instance factors, or nullptr
   const double* bvec;                     // [n][BS]
   double *x64, *r64;                      // [n][BS]
   float *x, *r, *z, *p, *q, *t;           // [n][BS]
@@ -187,7 +188,8 @@ __device__ __forceinline__ float fsai_row(const BatchArgs& a, int64_t i, int b, 
     for (int u = 0; u < U; ++u) {
       const bool ok = k + u < k1;
       c[u] = ok ? __ldg(a.col + k + u) : 0;
-      g[u] = ok ? __bfloat162float(a.g[k + u]) : 0.0f;
+      g[u] = !ok ? 0.0f
+                 : __bfloat162float(a.gb ? a.gb[(int64_t)(k + u) * BS + b] : a.g[k + u]);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) xv[u] = k + u < k1 ? X[(int64_t)c[u] * BS + b] : 0.0f;
@@ -413,6 +415,118 @@ pcg_batched_persistent(BatchArgs a) {
 }
 
 // ------------------------------------------------------------ set-up
+// Per-instance FSAI factors for the batched solve (same definition as the
+// single-instance factor: row i solves L_b[P_i, P_i] g = e_i and stores
+// g / sqrt(g_i)), computed in FP32 from the edge form of L_b and stored in
+// BF16 with the instances contiguous per entry.  A group of BS threads
+// handles one row, thread b instance b, each with the packed lower triangle
+// of its block in shared memory (k <= kBFsaiMax).  Longer rows keep the
+// shared factor of the uncracked operator.
+constexpr int kBFsaiMax = 16;
+constexpr int kBFsaiTpb = 256;
+constexpr int kBPacked = kBFsaiMax * (kBFsaiMax + 1) / 2;
+
+__device__ __forceinline__ int btri(int r, int c) { return r * (r + 1) / 2 + c; }
+
+__global__ void __launch_bounds__(kBFsaiTpb)
+batch_fsai_kernel(int64_t n, int BS, int states, const int32_t* __restrict__ rowptr,
+                  const int32_t* __restrict__ col, const int32_t* __restrict__ dpos,
+                  const int32_t* __restrict__ eid, const int32_t* __restrict__ pos_up,
+                  const uint8_t* __restrict__ tag, const float* __restrict__ w32,
+                  const uint8_t* __restrict__ fc, const __nv_bfloat16* __restrict__ g0,
+                  __nv_bfloat16* __restrict__ gb) {
+  extern __shared__ float bsm[];
+  float* A = bsm + threadIdx.x;                                  // stride kBFsaiTpb
+  int32_t* P = reinterpret_cast<int32_t*>(bsm + kBPacked * kBFsaiTpb) + threadIdx.x;
+  const int stride = kBFsaiTpb;
+  const int b = threadIdx.x % BS;
+  const int rpb = kBFsaiTpb / BS;
+  const int state = states ? b : 0;
+  for (int64_t i = (int64_t)blockIdx.x * rpb + threadIdx.x / BS; i < n;
+       i += (int64_t)gridDim.x * rpb) {
+    const int32_t k0 = rowptr[i], kd = dpos[i];
+    const int k = kd - k0 + 1;
+    if (k > kBFsaiMax) {   // this row's lower part and its transposed slots
+      for (int32_t kk = k0; kk <= kd; ++kk) {
+        gb[(int64_t)kk * BS + b] = g0[kk];
+        if (kk < kd) gb[(int64_t)pos_up[eid[kk]] * BS + b] = g0[pos_up[eid[kk]]];
+      }
+      continue;
+    }
+    for (int q = 0; q < k; ++q) P[q * stride] = col[k0 + q];
+    // gather L_b[P, P] (edge form; Dirichlet rows/columns eliminated)
+    float dmax = 0.0f;
+    for (int q = 0; q < k; ++q) {
+      const int32_t r = P[q * stride];
+      for (int c = 0; c < q; ++c) A[btri(q, c) * stride] = 0.0f;
+      if (tag[r] == DEC_NODE_DIRICHLET) { A[btri(q, q) * stride] = 1.0f; dmax = fmaxf(dmax, 1.0f); continue; }
+      float dsum = 0.0f;
+      int c = 0;
+      for (int32_t kk = rowptr[r]; kk < rowptr[r + 1]; ++kk) {
+        const float m = (int)fc[kk] > state ? w32[kk] : 0.0f;
+        dsum += m;
+        const int32_t cc = col[kk];
+        if (kk < dpos[r]) {            // lower part of row r: columns < r
+          while (c < q && P[c * stride] < cc) ++c;
+          if (c < q && P[c * stride] == cc && tag[cc] != DEC_NODE_DIRICHLET)
+            A[btri(q, c) * stride] = -m;
+        }
+      }
+      A[btri(q, q) * stride] = dsum == 0.0f ? 1.0f : dsum;
+      dmax = fmaxf(dmax, A[btri(q, q) * stride]);
+    }
+    // Cholesky in place; a pivot <= 1e-6 max(diag) marks a singular block,
+    // which is shifted by 1e-5 max(diag) and factored again
+    bool ok = true;
+    for (int pass = 0; pass < 2; ++pass) {
+      ok = true;
+      for (int c = 0; c < k && ok; ++c) {
+        const float d = A[btri(c, c) * stride];
+        if (!(d > (pass == 0 ? 1e-6f * dmax : 0.0f))) { ok = false; break; }
+        const float lc = sqrtf(d), inv = 1.0f / lc;
+        A[btri(c, c) * stride] = lc;
+        for (int r = c + 1; r < k; ++r) A[btri(r, c) * stride] *= inv;
+        for (int r = c + 1; r < k; ++r) {
+          const float lrc = A[btri(r, c) * stride];
+          for (int q = c + 1; q <= r; ++q) A[btri(r, q) * stride] -= lrc * A[btri(q, c) * stride];
+        }
+      }
+      if (ok || pass == 1) break;
+      // rebuild with a shift (the gather again, diagonal + shift)
+      for (int q = 0; q < k; ++q) {
+        const int32_t r = P[q * stride];
+        for (int c = 0; c < q; ++c) A[btri(q, c) * stride] = 0.0f;
+        if (tag[r] == DEC_NODE_DIRICHLET) { A[btri(q, q) * stride] = 1.0f + 1e-5f * dmax; continue; }
+        float dsum = 0.0f;
+        int c = 0;
+        for (int32_t kk = rowptr[r]; kk < rowptr[r + 1]; ++kk) {
+          const float m = (int)fc[kk] > state ? w32[kk] : 0.0f;
+          dsum += m;
+          const int32_t cc = col[kk];
+          if (kk < dpos[r]) {
+            while (c < q && P[c * stride] < cc) ++c;
+            if (c < q && P[c * stride] == cc && tag[cc] != DEC_NODE_DIRICHLET)
+              A[btri(q, c) * stride] = -m;
+          }
+        }
+        A[btri(q, q) * stride] = (dsum == 0.0f ? 1.0f : dsum) + 1e-5f * dmax;
+      }
+    }
+    // C^T g = e_k, g_j over the used diagonal slot
+    for (int j = k - 1; j >= 0; --j) {
+      float sum = (j == k - 1) ? 1.0f : 0.0f;
+      for (int r = j + 1; r < k; ++r) sum -= A[btri(r, j) * stride] * A[btri(r, r) * stride];
+      A[btri(j, j) * stride] = ok ? sum / A[btri(j, j) * stride] : 0.0f;
+    }
+    for (int q = 0; q < k; ++q) {
+      const __nv_bfloat16 gq = ok ? __float2bfloat16_rn(A[btri(q, q) * stride]) : g0[k0 + q];
+      gb[(int64_t)(k0 + q) * BS + b] = gq;
+      if (q < k - 1) gb[(int64_t)pos_up[eid[k0 + q]] * BS + b] = gq;
+    }
+  }
+}
+
+
 // per-entry edge data for the edge form: *1 (FP32, FP64) and first crack
 // state of the entry's edge; the diagonal slot gets w = 0, never cut
 __global__ void batch_entries_kernel(int64_t nnz, const int32_t* __restrict__ eid,
@@ -518,6 +632,25 @@ dec_status batch_setup(dec_ctx* ctx) {
   batch_rhs_unpack_kernel<<<g3, 256, 0, s>>>(n, B, BS, ctx->bb.p, ctx->b.p);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 3;
+  if (ctx->n_scales > 1) {
+    // crack states change L per instance: one FSAI factor per state
+    DEC_TRY(ctx->bgb.ensure((size_t)nnz * BS));
+    const size_t smem = (size_t)kBPacked * kBFsaiTpb * sizeof(float) +
+                        (size_t)kBFsaiMax * kBFsaiTpb * sizeof(int32_t);
+    DEC_TRY(cudaFuncSetAttribute(batch_fsai_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    const int rpb = kBFsaiTpb / BS;
+    const unsigned gf = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((n + rpb - 1) / rpb, (int64_t)ctx->num_sms * 8));
+    batch_fsai_kernel<<<gf, kBFsaiTpb, smem, s>>>(
+        n, BS, 1, ctx->rowptr.p, ctx->col.p, ctx->dpos.p, ctx->eid.p, ctx->pos_up.p,
+        ctx->tag.p, ctx->bw32.p, ctx->bfc.p, ctx->bg16.p, ctx->bgb.p);
+    DEC_TRY(cudaGetLastError());
+    ctx->launches += 1;
+    ctx->batch_per_instance = true;
+  } else {
+    ctx->batch_per_instance = false;   // Dirichlet sets share L and its factor
+  }
   return DEC_OK;
 }
 
@@ -558,6 +691,7 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   a.fc = ctx->bfc.p;
   a.states = ctx->n_scales > 1;
   a.g = ctx->bg16.p;
+  a.gb = ctx->batch_per_instance ? ctx->bgb.p : nullptr;
   a.bvec = ctx->bb.p;
   a.x64 = ctx->bx64.p;
   a.r64 = ctx->br64.p;

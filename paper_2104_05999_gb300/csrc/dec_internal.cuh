@@ -123,7 +123,7 @@ struct dec_ctx {
   dec::DevBuf<double> dinv64;      // [B][n]
   // solver state
   dec::DevBuf<double> x64, r64, z64, p64, q64, t64, u;  // u: [B][n] result
-  dec::DevBuf<float> x32, r32, z32, p32, q32, t32;
+  dec::DevBuf<float> x32, r32, z32, p32, q32, t32, r32b, p32b;
   dec::DevBuf<double> partial;     // [kRedSlots][reduce_grid]
   dec::DevBuf<unsigned> ticket;
   dec::DevBuf<dec::CgScalars> cg;
@@ -140,7 +140,8 @@ struct dec_ctx {
   dec::DevBuf<float> bw32;
   dec::DevBuf<double> bw64, bb, bx64, br64, bpartial;
   dec::DevBuf<uint8_t> bfc;
-  dec::DevBuf<__nv_bfloat16> bg16;
+  dec::DevBuf<__nv_bfloat16> bg16, bgb;   // shared factor, per-instance factors
+  bool batch_per_instance = false;
   dec::DevBuf<float> bx, br, bz, bp, bq, bt;
   std::vector<int> iters_host;
   std::vector<double> relres_host;
@@ -158,14 +159,14 @@ struct dec_ctx {
     dinv32.release(); dinv64.release(); x64.release();
     r64.release(); z64.release(); p64.release(); q64.release(); t64.release();
     u.release(); x32.release(); r32.release(); z32.release(); p32.release();
-    q32.release(); t32.release(); partial.release(); ticket.release();
+    q32.release(); t32.release(); r32b.release(); p32b.release(); partial.release(); ticket.release();
     cg.release(); out3.release(); flush.release();
     sellL.release(); sellLo.release(); sellUp.release(); sL64.release();
     sGlo64.release(); sGup64.release(); sL32.release(); sGlo16.release();
     sGup16.release(); big_rows.release(); coop.release(); bw32.release();
     bw64.release(); bb.release(); bx64.release(); br64.release(); bpartial.release();
     bfc.release(); bg16.release(); bx.release(); br.release(); bz.release();
-    bp.release(); bq.release(); bt.release();
+    bp.release(); bq.release(); bt.release(); bgb.release();
   }
 
   dec_status fail(dec_status s, const std::string& what) {

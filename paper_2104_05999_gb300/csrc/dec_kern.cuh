@@ -63,3 +63,4 @@ __device__ __forceinline__ VT sell_row(const SellArg<MT>& A, int64_t s, int lane
 }
 
 }  // namespace dec
+

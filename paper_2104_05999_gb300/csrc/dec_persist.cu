@@ -16,6 +16,7 @@
 #include "dec_kern.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace dec {
 
@@ -33,6 +34,7 @@ struct PersistArgs {
   const double* b;
   double *x64, *r64;
   float *x, *r, *z, *p, *q, *t;
+  float *r2, *p2;             // second buffers of r and p
   double* partial;            // [4][gridDim.x]
   unsigned* bar;              // [0] arrivals, [1] generation
   int* status;                // [0] error, [1] iterations, [2] outcome
@@ -109,6 +111,52 @@ __device__ __forceinline__ bool grid_sum(const T (&v)[NV], double (&tot)[NV],
   return true;
 }
 
+// Row sum over the lane's row of slice s with the gathered operand formed on
+// the fly: sum_j a_j * (X[c_j] + coef * Y[c_j]).  Used to fuse the vector
+// update that produced the operand into the product that consumes it (the
+// owner of row c computes the same fmaf for its own entry, so both agree).
+template <typename MT>
+__device__ __forceinline__ float sell_row2(const SellArg<MT>& A, int64_t s, int lane,
+                                           const float* __restrict__ X,
+                                           const float* __restrict__ Y, float coef) {
+  constexpr int U = 8;
+  const int32_t base = __ldg(A.sptr + s);
+  const int32_t w = (__ldg(A.sptr + s + 1) - base) >> 5;
+  const int32_t* __restrict__ cp = A.col + base + lane;
+  const MT* __restrict__ vp = A.val + base + lane;
+  float acc = 0.0f;
+  for (int32_t j = 0; j < w; j += U) {
+    int32_t c[U];
+    MT av[U];
+    float xv[U], yv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = j + u < w;
+      c[u] = ok ? __ldg(cp + 32 * (j + u)) : 0;
+      av[u] = ok ? vp[32 * (j + u)] : MT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      xv[u] = j + u < w ? X[c[u]] : 0.0f;
+      yv[u] = j + u < w ? Y[c[u]] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j + u < w) acc = fma_(av[u], fmaf(coef, yv[u], xv[u]), acc);
+  }
+  return acc;
+}
+
+// One CG iteration is three phases separated by the three grid reductions
+// it needs (p.q, r.r, r.z):
+//   A: p_k = z + beta p_{k-1} (own rows) and q = L p_k, gathering z and
+//      p_{k-1} so that p_k need not be complete first;
+//   B: r_{k+1} = r_k - alpha q, x += alpha p_k (own rows) and t = G r_{k+1},
+//      gathering r_k and q;
+//   C: z = G^T t and r.z.
+// p and r alternate between two buffers (a phase gathers the old vector while
+// owners write the new one).  With Jacobi, B computes z = r / diag directly
+// and C disappears.
 template <bool JACOBI>
 __global__ void __launch_bounds__(kPBlock, 1)
 pcg_mixed_persistent(PersistArgs a) {
@@ -118,8 +166,6 @@ pcg_mixed_persistent(PersistArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = gtid >> 5, nwarps = gstride >> 5;
   int* err = a.status;
-  // scalars derived from reductions: thread 0 computes, the block reads
-  // (one FP64 division per block instead of one per thread)
   __shared__ float s_scal;
   __shared__ int s_flag;
   auto finish = [&](int outcome, int iters, double rr, double bb) {
@@ -128,6 +174,19 @@ pcg_mixed_persistent(PersistArgs a) {
       a.status[2] = outcome;
       a.result[0] = rr;
       a.result[1] = bb;
+    }
+  };
+  float* P[2] = {a.p, a.p2};
+  float* R[2] = {a.r, a.r2};
+  int cur = 0;
+  // one slice per warp at a time; the gathered operand is X[c] (+ coef *
+  // Y[c] when Y is given).  (Interleaving two slices per warp needed more
+  // than the 64 registers a 1024-thread block allows and ran slower.)
+  auto slices = [&](const auto& A, auto&& body, const float* X, const float* Y, float coef) {
+    for (int64_t s = gwarp; s < A.nslices; s += nwarps) {
+      const float acc = Y ? sell_row2(A, s, lane, X, Y, coef) : sell_row(A, s, lane, X);
+      const int32_t r0 = __ldg(A.perm + 32 * s + lane);
+      if (r0 >= 0) body(r0, acc);
     }
   };
 
@@ -143,6 +202,7 @@ pcg_mixed_persistent(PersistArgs a) {
       a.r[i] = (float)bi;
       a.x[i] = 0.0f;
       a.p[i] = 0.0f;
+      a.p2[i] = 0.0f;
       bb += bi * bi;
     }
     v1[0] = bb;
@@ -153,129 +213,120 @@ pcg_mixed_persistent(PersistArgs a) {
   double rr64 = bnorm2, best = bnorm2, rz = 0.0;
   double tol2 = a.seg2 * rr64;
   int iters = 0, stall = 0, restart = 1;
+  float beta = 0.0f;
 
   for (;;) {
-    // ---- (re)start of a segment: z = M r, beta, p = z + beta p
+    // ---- segment start: z = M r (from R[cur]), r.z, beta
     {
       float v[1] = {0.0f};
       double t[1];
+      const float* rc = R[cur];
       if (JACOBI) {
         float acc = 0.0f;
         for (int64_t i = gtid; i < n; i += gstride) {
-          const float zi = a.dinv[i] * a.r[i];
+          const float zi = a.dinv[i] * rc[i];
           a.z[i] = zi;
-          acc = fmaf(a.r[i], zi, acc);
+          acc = fmaf(rc[i], zi, acc);
         }
         v[0] = acc;
       } else {
-        for (int64_t s = gwarp; s < a.Glo.nslices; s += nwarps) {
-          const int32_t row = __ldg(a.Glo.perm + 32 * s + lane);
-          const float acc = sell_row(a.Glo, s, lane, a.r);
-          if (row >= 0) a.t[row] = acc;
-        }
+        slices(a.Glo, [&](int32_t row, float acc) { a.t[row] = acc; }, rc,
+              (const float*)nullptr, 0.0f);
         if (!grid_sync(a.bar, err)) return;
         float acc2 = 0.0f;
-        for (int64_t s = gwarp; s < a.Gup.nslices; s += nwarps) {
-          const int32_t row = __ldg(a.Gup.perm + 32 * s + lane);
-          const float acc = sell_row(a.Gup, s, lane, a.t);
-          if (row >= 0) {
-            a.z[row] = acc;
-            acc2 = fmaf(a.r[row], acc, acc2);
-          }
-        }
+        slices(a.Gup, [&](int32_t row, float acc) {
+          a.z[row] = acc;
+          acc2 = fmaf(rc[row], acc, acc2);
+        }, a.t, (const float*)nullptr, 0.0f);
         v[0] = acc2;
       }
       if (!grid_sum<1>(v, t, a.partial, parity, a.bar, err)) return;
-      if (threadIdx.x == 0) s_scal = restart ? 0.0f : (float)(t[0] / rz);
+      if (threadIdx.x == 0) s_scal = (restart || rz == 0.0) ? 0.0f : (float)(t[0] / rz);
       __syncthreads();
+      beta = s_scal;
       rz = t[0];
-      const float fb = s_scal;
-      for (int64_t i = gtid; i < n; i += gstride) a.p[i] = fmaf(fb, a.p[i], a.z[i]);
-      if (!grid_sync(a.bar, err)) return;
     }
     // ---- FP32 iterations until the residual has dropped by seg2
     int breakdown = 0;
     for (;;) {
-      // q = A p, p.q
-      float v[2] = {0.0f, 0.0f};
-      double t[2];
-      float vq[1];
-      double tq[1];
+      const int nxt = cur ^ 1;
+      // A: p_k = z + beta p_{k-1}, q = L p_k, p_k . q
       {
+        const float* pold = P[cur];
+        float* pnew = P[nxt];
         float acc2 = 0.0f;
-        for (int64_t s = gwarp; s < a.A32.nslices; s += nwarps) {
-          const int32_t row = __ldg(a.A32.perm + 32 * s + lane);
-          const float acc = sell_row(a.A32, s, lane, a.p);
-          if (row >= 0) {
-            a.q[row] = acc;
-            acc2 = fmaf(a.p[row], acc, acc2);
-          }
+        slices(a.A32, [&](int32_t row, float qi) {
+          const float pi = fmaf(beta, pold[row], a.z[row]);
+          pnew[row] = pi;
+          a.q[row] = qi;
+          acc2 = fmaf(pi, qi, acc2);
+        }, a.z, pold, beta);
+        float vq[1] = {acc2};
+        double tq[1];
+        if (!grid_sum<1>(vq, tq, a.partial, parity, a.bar, err)) return;
+        if (threadIdx.x == 0) {
+          const double pq = tq[0];
+          s_flag = (!(pq > 0.0) || !isfinite(pq)) ? 1 : 0;
+          s_scal = s_flag ? 0.0f : (float)(rz / pq);
         }
-        vq[0] = acc2;
+        __syncthreads();
       }
-      if (!grid_sum<1>(vq, tq, a.partial, parity, a.bar, err)) return;
-      if (threadIdx.x == 0) {
-        const double pq = tq[0];
-        s_flag = (!(pq > 0.0) || !isfinite(pq)) ? 1 : 0;
-        s_scal = s_flag ? 0.0f : (float)(rz / pq);
-      }
-      __syncthreads();
-      if (s_flag) { breakdown = 1; break; }
+      if (s_flag) { breakdown = 1; cur = nxt; break; }   // p_k is in P[nxt]
       const float alpha = s_scal;
-      // x += alpha p, r -= alpha q, r.r (and Jacobi z, r.z)
+      // B: r_{k+1} = r_k - alpha q, x += alpha p_k, t = G r_{k+1}, r.r
+      float rr = 0.0f, rzj = 0.0f;
       {
-        float rr = 0.0f, rzj = 0.0f;
-        for (int64_t i = gtid; i < n; i += gstride) {
-          const float ri = fmaf(-alpha, a.q[i], a.r[i]);
-          a.x[i] = fmaf(alpha, a.p[i], a.x[i]);
-          a.r[i] = ri;
-          rr = fmaf(ri, ri, rr);
-          if (JACOBI) {
+        const float* rold = R[cur];
+        float* rnew = R[nxt];
+        const float* pk = P[nxt];
+        if (JACOBI) {
+          for (int64_t i = gtid; i < n; i += gstride) {
+            const float ri = fmaf(-alpha, a.q[i], rold[i]);
+            rnew[i] = ri;
+            a.x[i] = fmaf(alpha, pk[i], a.x[i]);
+            rr = fmaf(ri, ri, rr);
             const float zi = a.dinv[i] * ri;
             a.z[i] = zi;
             rzj = fmaf(ri, zi, rzj);
           }
+        } else {
+          slices(a.Glo, [&](int32_t row, float ti) {
+            const float ri = fmaf(-alpha, a.q[row], rold[row]);
+            rnew[row] = ri;
+            a.x[row] = fmaf(alpha, pk[row], a.x[row]);
+            a.t[row] = ti;
+            rr = fmaf(ri, ri, rr);
+          }, rold, (const float*)a.q, -alpha);
         }
-        v[0] = rr;
-        v[1] = rzj;
       }
-      if (!grid_sum<2>(v, t, a.partial, parity, a.bar, err)) return;
+      float v2[2] = {rr, rzj};
+      double t2[2];
+      if (!grid_sum<2>(v2, t2, a.partial, parity, a.bar, err)) return;
+      cur = nxt;
       ++iters;
-      const double rr = t[0];
-      if (rr <= tol2 || iters >= a.max_iter || !isfinite(rr)) break;
+      if (t2[0] <= tol2 || iters >= a.max_iter || !isfinite(t2[0])) break;
       double rz_new;
       if (JACOBI) {
-        rz_new = t[1];
+        rz_new = t2[1];
       } else {
-        for (int64_t s = gwarp; s < a.Glo.nslices; s += nwarps) {
-          const int32_t row = __ldg(a.Glo.perm + 32 * s + lane);
-          const float acc = sell_row(a.Glo, s, lane, a.r);
-          if (row >= 0) a.t[row] = acc;
-        }
-        if (!grid_sync(a.bar, err)) return;
+        // C: z = G^T t, r.z
         float acc2 = 0.0f;
-        for (int64_t s = gwarp; s < a.Gup.nslices; s += nwarps) {
-          const int32_t row = __ldg(a.Gup.perm + 32 * s + lane);
-          const float acc = sell_row(a.Gup, s, lane, a.t);
-          if (row >= 0) {
-            a.z[row] = acc;
-            acc2 = fmaf(a.r[row], acc, acc2);
-          }
-        }
+        const float* rcur = R[cur];
+        slices(a.Gup, [&](int32_t row, float zi) {
+          a.z[row] = zi;
+          acc2 = fmaf(rcur[row], zi, acc2);
+        }, a.t, (const float*)nullptr, 0.0f);
         float vz[1] = {acc2};
         double tz[1];
         if (!grid_sum<1>(vz, tz, a.partial, parity, a.bar, err)) return;
         rz_new = tz[0];
       }
-      __syncthreads();
       if (threadIdx.x == 0) s_scal = (float)(rz_new / rz);
       __syncthreads();
-      const float beta = s_scal;
+      beta = s_scal;
       rz = rz_new;
-      for (int64_t i = gtid; i < n; i += gstride) a.p[i] = fmaf(beta, a.p[i], a.z[i]);
-      if (!grid_sync(a.bar, err)) return;
     }
-    // ---- reliable update: x64 += x, x = 0; r64 = b - L x64; r = (float) r64
+    // ---- reliable update: x64 += x, x = 0; r64 = b - L x64; R[cur] = (float) r64
     for (int64_t i = gtid; i < n; i += gstride) {
       a.x64[i] += (double)a.x[i];
       a.x[i] = 0.0f;
@@ -283,13 +334,14 @@ pcg_mixed_persistent(PersistArgs a) {
     if (!grid_sync(a.bar, err)) return;
     {
       double rr = 0.0;
+      float* rc = R[cur];
       for (int64_t s = gwarp; s < a.A64.nslices; s += nwarps) {
         const int32_t row = __ldg(a.A64.perm + 32 * s + lane);
         const double acc = sell_row(a.A64, s, lane, a.x64);
         if (row >= 0) {
           const double ri = a.b[row] - acc;
           a.r64[row] = ri;
-          a.r[row] = (float)ri;
+          rc[row] = (float)ri;
           rr = fma(ri, ri, rr);
         }
       }
@@ -341,6 +393,9 @@ dec_status solve_mixed_persistent(dec_ctx* ctx, int inst, double rtol, int max_i
   a.r64 = ctx->r64.p;
   a.x = ctx->x32.p; a.r = ctx->r32.p; a.z = ctx->z32.p; a.p = ctx->p32.p;
   a.q = ctx->q32.p; a.t = ctx->t32.p;
+  DEC_TRY(ctx->r32b.ensure(n));
+  DEC_TRY(ctx->p32b.ensure(n));
+  a.r2 = ctx->r32b.p; a.p2 = ctx->p32b.p;
   a.partial = ctx->partial.p;
   a.bar = bar;
   a.status = status;
