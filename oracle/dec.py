@@ -26,6 +26,9 @@ Readings of the paper this oracle takes (each also listed with the library):
     reproduced exactly on any mesh, as Sec. 2.5 and Sec. 3.1 report;
   * the 1e-8 Hodge limiter of Sec. 3.1 is not applied: the node form divides
     only by primal edge lengths;
+  * a per-tet conductivity becomes one value per dual face, the mean of k_T
+    over the tets around the edge weighted by the unsigned areas of their
+    parts of the face (signed weights would give negative conductances);
   * a crack disc that cuts any sub-triangle of an edge's dual face zeroes
     that edge's whole *1 entry;
   * the Krylov stopping rule is ||b - L x||_2 / ||b||_2 <= rtol with x0 = 0.
@@ -184,18 +187,32 @@ def hodge_pieces(xyz: np.ndarray, tets: np.ndarray):
 
 def hodge_star1(xyz, tets, E, t2e, k=None, cut=None):
     """Diagonal Hodge star on primal 1-cells (Sec. 2.1): *1[e] = |*e| / |e|,
-    the signed circumcentric dual-face area over the edge length.  The
-    conductivity k_T of each tet scales that tet's share of the dual face
-    (conductivity lives on dual 2-cells, Sec. 2.1).  Edges marked in ``cut``
-    get *1 = 0 (a crack makes a dual face insulating, Sec. 2.5)."""
+    the signed circumcentric dual-face area over the edge length, times the
+    conductivity of the dual face.
+
+    Conductivity is one value per dual 2-cell (Sec. 2.1).  A per-tet field
+    k_T is carried onto the dual face of e as the mean of k_T over the tets
+    around e, weighted by the unsigned areas of their parts of that face:
+        kappa_e = sum_T k_T |*e cap T| / sum_T |*e cap T|,
+    (|*e cap T| summed over the two sub-triangles of the part), so constant k
+    scales *1 and a cell-wise positive k keeps every conductance >= 0 where
+    the geometric *1 is.  Edges marked in ``cut`` get *1 = 0 (a crack makes a
+    dual face insulating, Sec. 2.5)."""
     area, _ = hodge_pieces(xyz, tets)
     piece = area.sum(axis=2)                       # [m, 6]
-    if k is not None:
-        piece = piece * np.asarray(k)[:, None]
     dual_area = np.bincount(t2e.reshape(-1), weights=piece.reshape(-1),
                             minlength=len(E))
     length = np.linalg.norm(xyz[E[:, 1]] - xyz[E[:, 0]], axis=1)
     w = dual_area / length
+    if k is not None:
+        part = np.abs(area).sum(axis=2)            # unsigned part of *e in T
+        num = np.bincount(t2e.reshape(-1),
+                          weights=(part * np.asarray(k)[:, None]).reshape(-1),
+                          minlength=len(E))
+        den = np.bincount(t2e.reshape(-1), weights=part.reshape(-1),
+                          minlength=len(E))
+        kappa = np.divide(num, den, out=np.zeros_like(num), where=den > 0)
+        w = kappa * w
     if cut is not None:
         w = np.where(cut, 0.0, w)
     return w

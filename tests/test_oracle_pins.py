@@ -169,20 +169,50 @@ def test_dual_volumes_tile_the_cube(name, N):
     np.testing.assert_allclose(np.diag(M), 1.0, atol=1e-13)
 
 
-def test_conductivity_scales_each_tets_share():
-    wl = make_workload("lognormal64", N=5)
+def test_conductivity_is_one_value_per_dual_face():
+    # Sec. 2.1: conductivity belongs to the dual 2-cell, so *1 with a
+    # per-tet field is the geometric *1 times one kappa_e per edge, a
+    # positive-weighted mean of the k_T around the edge
+    wl = make_workload("lognormal64", N=6)
     E, t2e = O.edge_list(wl.tets)
-    k = wl.k
-    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e, k)
-    # same result from per-tet single-tet stars summed with weight k_T
-    acc = np.zeros(len(E))
-    for t in range(wl.m):
-        T = wl.tets[t:t + 1]
-        e1, s1 = O.edge_list(T)
-        w1 = O.hodge_star1(wl.xyz, T, e1, s1)
-        for s in range(6):
-            acc[t2e[t, s]] += k[t] * w1[s1[0, s]]
-    np.testing.assert_allclose(w, acc, rtol=1e-12, atol=1e-16)
+    w0 = O.hodge_star1(wl.xyz, wl.tets, E, t2e)
+    # constant k scales every entry
+    wc = O.hodge_star1(wl.xyz, wl.tets, E, t2e, np.full(wl.m, 3.7))
+    np.testing.assert_allclose(wc, 3.7 * w0, rtol=1e-15, atol=0)
+    # kappa_e lies between the smallest and largest k_T around e, and a
+    # conductance is never negative where the geometric *1 is not (the mesh
+    # has pieces of both signs, so a signed weighting would break this)
+    area, _ = O.hodge_pieces(wl.xyz, wl.tets)
+    assert (area < 0).any()
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e, wl.k)
+    kmin = np.full(len(E), np.inf)
+    kmax = np.zeros(len(E))
+    np.minimum.at(kmin, t2e.reshape(-1), np.repeat(wl.k, 6))
+    np.maximum.at(kmax, t2e.reshape(-1), np.repeat(wl.k, 6))
+    big = w0 > 1e-10 * w0.max()
+    kap = w[big] / w0[big]
+    assert (kap >= kmin[big] * (1 - 1e-12)).all()
+    assert (kap <= kmax[big] * (1 + 1e-12)).all()
+    assert (w0 >= 0).all() and (w >= 0).all()
+
+
+def test_layered_conductivity_gives_the_series_solution():
+    # two layers x < 1/2 (k1) and x > 1/2 (k2) between the Dirichlet faces:
+    # the exact field is piecewise linear with k1 s1 = k2 s2 and the
+    # effective conductivity is the series value 2 k1 k2 / (k1 + k2)
+    k1, k2 = 1.0, 4.0
+    wl = make_workload("kuhn9", N=5)                 # x = 1/2 is a node plane
+    cx = wl.xyz[wl.tets, 0].mean(axis=1)
+    k = np.where(cx < 0.5, k1, k2)
+    out = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=k,
+                       precond="jacobi", rtol=1e-14)
+    Tm = k1 / (k1 + k2)
+    x = wl.xyz[:, 0]
+    exact = np.where(x <= 0.5, 1.0 - (1.0 - Tm) * 2.0 * x,
+                     Tm * 2.0 * (1.0 - x))
+    np.testing.assert_allclose(out["T"][0], exact, atol=1e-12)
+    assert out["q_in"][0] == pytest.approx(2 * k1 * k2 / (k1 + k2), rel=1e-12)
+    assert out["q_out"][0] == pytest.approx(2 * k1 * k2 / (k1 + k2), rel=1e-12)
 
 
 # ------------------------------------------------------------------ cracks
