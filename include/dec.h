@@ -70,9 +70,12 @@ enum { DEC_NODE_FREE = 0, DEC_NODE_DIRICHLET = 1, DEC_NODE_NEUMANN = 2 };
 enum {
   DEC_PRECOND_JACOBI = 0,       /* 1 / L_ii, per instance                     */
   DEC_PRECOND_FSAI = 1,         /* FSAI factor per instance (value set)       */
-  DEC_PRECOND_FSAI_SHARED = 2   /* one FSAI factor, of the uncracked operator,
-                                   shared by every instance; prepares the
-                                   batched solve (DEC_MODE_MIXED_BATCHED)     */
+  DEC_PRECOND_FSAI_SHARED = 2   /* prepares the batched solve
+                                   (DEC_MODE_MIXED_BATCHED): Dirichlet sets
+                                   share the FSAI factor of their common L;
+                                   crack states get one FP32-built BF16
+                                   factor each (rows longer than 16 keep the
+                                   uncracked operator's factor)               */
 };
 /* solve modes (dec_solve) */
 enum {
@@ -204,8 +207,9 @@ dec_status dec_get_hodge(dec_ctx* ctx, double* w, uint8_t* first_cut);
 
 /* CSR of L: rowptr [n_nodes+1] int32, col [nnz] int32, columns sorted,
  * diagonal included.  val [nnz] f64 and b [n_nodes] f64 of instance
- * `inst` (after DEC_PRECOND_FSAI_SHARED, val is the uncracked operator
- * shared by all instances, b is still per instance).  Any pointer may be
+ * `inst` (after DEC_PRECOND_FSAI_SHARED, val is the common operator of
+ * Dirichlet sets, or the uncracked operator for crack states; b is still
+ * per instance).  Any pointer may be
  * NULL.  Host or device buffers. */
 dec_status dec_get_csr(dec_ctx* ctx, int32_t inst, int32_t* rowptr,
                        int32_t* col, double* val, double* b);

@@ -232,8 +232,11 @@ dec_status dec_laplacian_build(dec_ctx* ctx, const double* T0, int32_t n_sets,
     DEC_TRY(ctx->dinv32.ensure((size_t)V * n));
   }
   if (shared) {
-    // one FSAI factor of the uncracked operator, per-entry edge data, b[n][BS]
-    DEC_TRY_STATUS(dec::build_values_uncracked(ctx));
+    // one shared FSAI factor (Dirichlet sets: of their common operator; crack
+    // states: of the uncracked one, the fallback of the per-state factors),
+    // per-entry edge data, b[n][BS]
+    if (ctx->n_scales > 1) DEC_TRY_STATUS(dec::build_values_uncracked(ctx));
+    else DEC_TRY_STATUS(dec::build_values(ctx, 0));
     DEC_TRY_STATUS(dec::build_precond(ctx, 0));
     DEC_TRY_STATUS(dec::batch_setup(ctx));
   } else {

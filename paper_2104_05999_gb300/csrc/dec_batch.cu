@@ -5,15 +5,17 @@
 //
 // The instances share L's sparsity; vectors are stored node-major with the
 // instances contiguous (X[i * BS + b], BS = padded instance count), so one
-// gathered neighbour row X[c][0..BS) is one coalesced load.  A group of BS
-// threads works on one row, thread b on instance b.  The operator of
-// instance b is applied in "edge form" from shared per-entry data (column,
-// *1 in FP32 and FP64, first crack state):
+// gathered neighbour row X[c][0..BS) is one coalesced load.  Each thread
+// handles four consecutive instances of a row (16-byte loads), so BS / 4
+// threads share a row and the per-entry structure is read once per four
+// instances.  The operator of instance b is applied in "edge form" from
+// shared per-entry data (column, *1 in FP32 and FP64, first crack state):
 //   (L_b x)_i = sum_k w_k [b < fc_k] (x_i - x_c),
 // which needs no per-instance values or diagonal (vectors are zero on
 // Dirichlet nodes, so those columns drop out; Dirichlet rows and rows whose
-// weights are all zero in instance b are identity rows).  All instances use
-// one FSAI factor, that of the uncracked operator.
+// weights are all zero in instance b are identity rows).  Dirichlet value
+// sets share the FSAI factor of L; crack states each get their own factor,
+// computed in FP32 and stored in BF16 with the instances contiguous.
 //
 // Per-instance convergence masks: an instance stops working once its FP64
 // residual reaches rtol; within a segment it is frozen once its FP32
@@ -99,27 +101,38 @@ struct BState {
   int count;                     // scratch: number of iterating instances
 };
 
-// Per-instance grid reduction of NV values; thread t contributes v[k] to
-// instance t % BS.  Results land in S.red[k][b], identical in every block.
+// Each thread works on four instances (one float4 of a node's row of a
+// batched vector): a row of BS instances is handled by TPR = BS / 4 threads.
+// The per-entry structure (column, weight, crack state) is loaded once per
+// four instances and the gathers are 16-byte loads.
+constexpr int kIPT = 4;
+
+// Per-instance grid reduction of NV quantities; thread t contributes v[k][j]
+// to instance 4 (t % TPR) + j.  Results land in S.red[k][b], identical in
+// every block.
 template <int NV>
-__device__ bool breduce(const double (&v)[NV], double* partial, int& parity, BState& S,
+__device__ bool breduce(const double (&v)[NV][kIPT], double* partial, int& parity, BState& S,
                         double* sh, int BS, unsigned* bar, int* err) {
   const int G = gridDim.x;
+  const int TPR = BS / kIPT;
   double* part = partial + (size_t)parity * 2 * G * BS;
   parity ^= 1;
-  const int per = kBBlock / BS;            // threads per instance in a block
+  const int rows = kBBlock / TPR;                 // threads sharing an instance quad
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    sh[threadIdx.x] = v[k];
+#pragma unroll
+    for (int j = 0; j < kIPT; ++j) sh[threadIdx.x * kIPT + j] = v[k][j];
     __syncthreads();
     if (threadIdx.x < BS) {
+      const int q = threadIdx.x / kIPT, j = threadIdx.x % kIPT;
       double s = 0.0;
-      for (int j = 0; j < per; ++j) s += sh[threadIdx.x + j * BS];
+      for (int m = 0; m < rows; ++m) s += sh[(q + m * TPR) * kIPT + j];
       part[((size_t)k * G + blockIdx.x) * BS + threadIdx.x] = s;
     }
     __syncthreads();
   }
   if (!bgrid_sync(bar, err)) return false;
+  const int per = kBBlock / BS;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     const int b = threadIdx.x % BS, slot = threadIdx.x / BS;
@@ -138,65 +151,127 @@ __device__ bool breduce(const double (&v)[NV], double* partial, int& parity, BSt
   return true;
 }
 
-// y = L_b x for row i, instance b; FP32 (T = float) or FP64.  Entries are
-// taken 8 at a time (8 column/weight/state loads, then 8 independent
-// gathers) to keep loads in flight.  The diagonal slot carries w = 0, so it
-// needs no test.
-template <typename T>
-__device__ __forceinline__ T edge_form_row(const BatchArgs& a, int64_t i, int b, int state,
-                                           const T* __restrict__ X, const T* __restrict__ w) {
-  constexpr int U = 8;
-  const int32_t k0 = a.rowptr[i], k1 = a.rowptr[i + 1];
-  const int BS = a.BS;
-  const T xi = X[i * BS + b];
-  if (a.tag[i] == DEC_NODE_DIRICHLET) return xi;
-  T acc = T(0), dsum = T(0);
-  for (int32_t k = k0; k < k1; k += U) {
-    int32_t c[U];
-    T m[U], xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool ok = k + u < k1;
-      c[u] = ok ? __ldg(a.col + k + u) : 0;
-      const T wk = ok ? __ldg(w + k + u) : T(0);
-      const int f = ok ? (int)__ldg(a.fc + k + u) : 0;
-      m[u] = f > state ? wk : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = k + u < k1 ? X[(int64_t)c[u] * BS + b] : T(0);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      dsum += m[u];
-      acc += m[u] * xv[u];
-    }
-  }
-  return dsum == T(0) ? xi : dsum * xi - acc;
+__device__ __forceinline__ float get4(const float4& v, int j) {
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set4(float4& v, int j, float x) {
+  if (j == 0) v.x = x; else if (j == 1) v.y = x; else if (j == 2) v.z = x; else v.w = x;
 }
 
-// FSAI halves with the shared factor (lower: G, upper: G^T), 8 at a time
-__device__ __forceinline__ float fsai_row(const BatchArgs& a, int64_t i, int b, bool lower,
-                                          const float* __restrict__ X) {
-  constexpr int U = 8;
-  const int32_t k0 = lower ? a.rowptr[i] : a.dpos[i];
-  const int32_t k1 = lower ? a.dpos[i] + 1 : a.rowptr[i + 1];
-  const int BS = a.BS;
-  float acc = 0.0f;
+// (L_b x)_i for the four instances 4q..4q+3 of row i (FP32).  Entries are
+// taken 4 at a time: structure loads, then 4 independent 16-byte gathers.
+// The diagonal slot carries w = 0, so it needs no test.
+__device__ __forceinline__ float4 edge_form4(const BatchArgs& a, int64_t i, int q,
+                                             const int (&st)[kIPT],
+                                             const float4* __restrict__ X) {
+  constexpr int U = 4;
+  const int TPR = a.BS / kIPT;
+  const float4 xi = X[i * TPR + q];
+  if (a.tag[i] == DEC_NODE_DIRICHLET) return xi;
+  const int32_t k0 = a.rowptr[i], k1 = a.rowptr[i + 1];
+  float acc[kIPT] = {0.f, 0.f, 0.f, 0.f}, dsum[kIPT] = {0.f, 0.f, 0.f, 0.f};
   for (int32_t k = k0; k < k1; k += U) {
     int32_t c[U];
-    float g[U], xv[U];
+    float wv[U];
+    int f[U];
+    float4 xv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool ok = k + u < k1;
       c[u] = ok ? __ldg(a.col + k + u) : 0;
-      g[u] = !ok ? 0.0f
-                 : __bfloat162float(a.gb ? a.gb[(int64_t)(k + u) * BS + b] : a.g[k + u]);
+      wv[u] = ok ? __ldg(a.w32 + k + u) : 0.0f;
+      f[u] = ok ? (int)__ldg(a.fc + k + u) : 0;
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = k + u < k1 ? X[(int64_t)c[u] * BS + b] : 0.0f;
+    for (int u = 0; u < U; ++u)
+      xv[u] = k + u < k1 ? X[(int64_t)c[u] * TPR + q] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc = fmaf(g[u], xv[u], acc);
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < kIPT; ++j) {
+        const float m = f[u] > st[j] ? wv[u] : 0.0f;
+        dsum[j] += m;
+        acc[j] = fmaf(m, get4(xv[u], j), acc[j]);
+      }
   }
-  return acc;
+  float4 y;
+#pragma unroll
+  for (int j = 0; j < kIPT; ++j)
+    set4(y, j, dsum[j] == 0.0f ? get4(xi, j) : fmaf(dsum[j], get4(xi, j), -acc[j]));
+  return y;
+}
+
+// The same in FP64 (the residual of a reliable update), x64 as double
+__device__ __forceinline__ void edge_form4_64(const BatchArgs& a, int64_t i, int q,
+                                              const int (&st)[kIPT],
+                                              const double* __restrict__ X, double (&y)[kIPT]) {
+  const int BS = a.BS;
+  const double* xi = X + i * BS + kIPT * q;
+  if (a.tag[i] == DEC_NODE_DIRICHLET) {
+#pragma unroll
+    for (int j = 0; j < kIPT; ++j) y[j] = xi[j];
+    return;
+  }
+  double acc[kIPT] = {0.0, 0.0, 0.0, 0.0}, dsum[kIPT] = {0.0, 0.0, 0.0, 0.0};
+  for (int32_t k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k) {
+    const int32_t c = __ldg(a.col + k);
+    const double wk = __ldg(a.w64 + k);
+    const int f = (int)__ldg(a.fc + k);
+    const double2 x01 = *reinterpret_cast<const double2*>(X + (int64_t)c * BS + kIPT * q);
+    const double2 x23 = *reinterpret_cast<const double2*>(X + (int64_t)c * BS + kIPT * q + 2);
+    const double xc[kIPT] = {x01.x, x01.y, x23.x, x23.y};
+#pragma unroll
+    for (int j = 0; j < kIPT; ++j) {
+      const double m = f > st[j] ? wk : 0.0;
+      dsum[j] += m;
+      acc[j] = fma(m, xc[j], acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kIPT; ++j) y[j] = dsum[j] == 0.0 ? xi[j] : fma(dsum[j], xi[j], -acc[j]);
+}
+
+// FSAI halves (lower: G, upper: G^T) for four instances; per-instance
+// factors (gb) or the shared one (g)
+__device__ __forceinline__ float4 fsai4(const BatchArgs& a, int64_t i, int q, bool lower,
+                                        const float4* __restrict__ X) {
+  constexpr int U = 4;
+  const int BS = a.BS, TPR = BS / kIPT;
+  const int32_t k0 = lower ? a.rowptr[i] : a.dpos[i];
+  const int32_t k1 = lower ? a.dpos[i] + 1 : a.rowptr[i + 1];
+  float acc[kIPT] = {0.f, 0.f, 0.f, 0.f};
+  for (int32_t k = k0; k < k1; k += U) {
+    int32_t c[U];
+    float g[U][kIPT];
+    float4 xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = k + u < k1;
+      c[u] = ok ? __ldg(a.col + k + u) : 0;
+      if (!ok) {
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) g[u][j] = 0.0f;
+      } else if (a.gb) {
+        const uint2 raw = *reinterpret_cast<const uint2*>(a.gb + (int64_t)(k + u) * BS + kIPT * q);
+        const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+        const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+        g[u][0] = __low2float(lo); g[u][1] = __high2float(lo);
+        g[u][2] = __low2float(hi); g[u][3] = __high2float(hi);
+      } else {
+        const float gs = __bfloat162float(a.g[k + u]);
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) g[u][j] = gs;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      xv[u] = k + u < k1 ? X[(int64_t)c[u] * TPR + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < kIPT; ++j) acc[j] = fmaf(g[u][j], get4(xv[u], j), acc[j]);
+  }
+  return make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
 // Dot-product accumulator: FP32 products folded into FP64 every 16 terms,
@@ -215,33 +290,49 @@ struct Acc2 {
 __global__ void __launch_bounds__(kBBlock, 1)
 pcg_batched_persistent(BatchArgs a) {
   __shared__ BState S;
-  __shared__ double sh[kBBlock];
-  const int BS = a.BS;
+  __shared__ double sh[kBBlock * kIPT];
+  const int BS = a.BS, TPR = BS / kIPT;
   const int64_t n = a.n;
-  const int b = threadIdx.x % BS;                       // this thread's instance
-  const int rpb = kBBlock / BS;                         // rows per block and pass
-  const int64_t row0 = (int64_t)blockIdx.x * rpb + threadIdx.x / BS;
+  const int q = threadIdx.x % TPR;                     // instance quad of this thread
+  const int rpb = kBBlock / TPR;                       // rows per block and pass
+  const int64_t row0 = (int64_t)blockIdx.x * rpb + threadIdx.x / TPR;
   const int64_t rstep = (int64_t)gridDim.x * rpb;
-  const int64_t ne = n * BS;
+  const int64_t nq = n * TPR;                          // float4 elements of a vector
   const int64_t e0 = (int64_t)blockIdx.x * kBBlock + threadIdx.x;
   const int64_t estep = (int64_t)gridDim.x * kBBlock;
-  const int state = a.states ? b : 0;
+  int st[kIPT];
+#pragma unroll
+  for (int j = 0; j < kIPT; ++j) st[j] = a.states ? kIPT * q + j : 0;
   int* err = a.status;
   int parity = 0;
+  float4* X = reinterpret_cast<float4*>(a.x);
+  float4* R = reinterpret_cast<float4*>(a.r);
+  float4* Z = reinterpret_cast<float4*>(a.z);
+  float4* Pv = reinterpret_cast<float4*>(a.p);
+  float4* Q = reinterpret_cast<float4*>(a.q);
+  float4* T = reinterpret_cast<float4*>(a.t);
+  auto act = [&](const int* flags, int j) { return flags[kIPT * q + j] != 0; };
+  auto any4 = [&](const int* flags) {
+    return flags[kIPT * q] | flags[kIPT * q + 1] | flags[kIPT * q + 2] | flags[kIPT * q + 3];
+  };
 
   // ---- start: x64 = 0, r64 = b, r = (float) b, x = p = 0, |b|^2 per instance
   {
-    double bb = 0.0;
-    for (int64_t e = e0; e < ne; e += estep) {
-      const double bi = a.bvec[e];
-      a.x64[e] = 0.0;
-      a.r64[e] = bi;
-      a.r[e] = (float)bi;
-      a.x[e] = 0.0f;
-      a.p[e] = 0.0f;
-      bb = fma(bi, bi, bb);
+    double v[1][kIPT] = {{0.0, 0.0, 0.0, 0.0}};
+    for (int64_t e = e0; e < nq; e += estep) {
+      float4 rf;
+#pragma unroll
+      for (int j = 0; j < kIPT; ++j) {
+        const double bi = a.bvec[e * kIPT + j];
+        a.x64[e * kIPT + j] = 0.0;
+        a.r64[e * kIPT + j] = bi;
+        set4(rf, j, (float)bi);
+        v[0][j] = fma(bi, bi, v[0][j]);
+      }
+      R[e] = rf;
+      X[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+      Pv[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    double v[1] = {bb};
     if (!breduce<1>(v, a.partial, parity, S, sh, BS, a.bar, err)) return;
   }
   if (threadIdx.x < BS) {
@@ -260,18 +351,22 @@ pcg_batched_persistent(BatchArgs a) {
 
   for (;;) {
     // ---- segment start for the active instances: z = M r, p = z + beta p
-    for (int64_t i = row0; i < n; i += rstep)
-      if (S.active[b]) a.t[i * BS + b] = fsai_row(a, i, b, true, a.r);
+    if (any4(S.active))
+      for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4(a, i, q, true, R);
     if (!bgrid_sync(a.bar, err)) return;
     {
-      Acc2 rz;
-      for (int64_t i = row0; i < n; i += rstep)
-        if (S.active[b]) {
-          const float zi = fsai_row(a, i, b, false, a.t);
-          a.z[i * BS + b] = zi;
-          rz.add(a.r[i * BS + b], zi);
+      Acc2 acc[kIPT];
+      if (any4(S.active))
+        for (int64_t i = row0; i < n; i += rstep) {
+          const float4 zi = fsai4(a, i, q, false, T);
+          Z[i * TPR + q] = zi;
+          const float4 ri = R[i * TPR + q];
+#pragma unroll
+          for (int j = 0; j < kIPT; ++j) acc[j].add(get4(ri, j), get4(zi, j));
         }
-      double v[1] = {rz.get()};
+      double v[1][kIPT];
+#pragma unroll
+      for (int j = 0; j < kIPT; ++j) v[0][j] = acc[j].get();
       if (!breduce<1>(v, a.partial, parity, S, sh, BS, a.bar, err)) return;
     }
     if (threadIdx.x < BS) {
@@ -282,21 +377,33 @@ pcg_batched_persistent(BatchArgs a) {
       S.iterating[i] = S.active[i];
     }
     __syncthreads();
-    for (int64_t e = e0; e < ne; e += estep)
-      if (S.active[b]) a.p[e] = fmaf(S.beta[b], a.p[e], a.z[e]);
+    if (any4(S.active)) {
+      float4 bt;
+#pragma unroll
+      for (int j = 0; j < kIPT; ++j) set4(bt, j, S.beta[kIPT * q + j]);
+      for (int64_t e = e0; e < nq; e += estep) {
+        const float4 zv = Z[e], pv = Pv[e];
+        Pv[e] = make_float4(fmaf(bt.x, pv.x, zv.x), fmaf(bt.y, pv.y, zv.y),
+                            fmaf(bt.z, pv.z, zv.z), fmaf(bt.w, pv.w, zv.w));
+      }
+    }
     if (!bgrid_sync(a.bar, err)) return;
 
     // ---- FP32 iterations until every working instance is frozen
     for (;;) {
       {
-        Acc2 pq;
-        for (int64_t i = row0; i < n; i += rstep)
-          if (S.iterating[b]) {
-            const float qi = edge_form_row<float>(a, i, b, state, a.p, a.w32);
-            a.q[i * BS + b] = qi;
-            pq.add(a.p[i * BS + b], qi);
+        Acc2 acc[kIPT];
+        if (any4(S.iterating))
+          for (int64_t i = row0; i < n; i += rstep) {
+            const float4 qi = edge_form4(a, i, q, st, Pv);
+            Q[i * TPR + q] = qi;
+            const float4 pi = Pv[i * TPR + q];
+#pragma unroll
+            for (int j = 0; j < kIPT; ++j) acc[j].add(get4(pi, j), get4(qi, j));
           }
-        double v[1] = {pq.get()};
+        double v[1][kIPT];
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) v[0][j] = acc[j].get();
         if (!breduce<1>(v, a.partial, parity, S, sh, BS, a.bar, err)) return;
       }
       if (threadIdx.x < BS) {
@@ -310,16 +417,25 @@ pcg_batched_persistent(BatchArgs a) {
       }
       __syncthreads();
       {
-        Acc2 rr;
-        for (int64_t e = e0; e < ne; e += estep)
-          if (S.iterating[b]) {
-            const float al = S.alpha[b];
-            const float ri = fmaf(-al, a.q[e], a.r[e]);
-            a.x[e] = fmaf(al, a.p[e], a.x[e]);
-            a.r[e] = ri;
-            rr.add(ri, ri);
+        Acc2 acc[kIPT];
+        if (any4(S.iterating)) {
+          float4 al;
+#pragma unroll
+          for (int j = 0; j < kIPT; ++j) set4(al, j, S.alpha[kIPT * q + j]);
+          for (int64_t e = e0; e < nq; e += estep) {
+            const float4 qv = Q[e], rv = R[e], pv = Pv[e], xv = X[e];
+            const float4 rn = make_float4(fmaf(-al.x, qv.x, rv.x), fmaf(-al.y, qv.y, rv.y),
+                                          fmaf(-al.z, qv.z, rv.z), fmaf(-al.w, qv.w, rv.w));
+            X[e] = make_float4(fmaf(al.x, pv.x, xv.x), fmaf(al.y, pv.y, xv.y),
+                               fmaf(al.z, pv.z, xv.z), fmaf(al.w, pv.w, xv.w));
+            R[e] = rn;
+#pragma unroll
+            for (int j = 0; j < kIPT; ++j) acc[j].add(get4(rn, j), get4(rn, j));
           }
-        double v[1] = {rr.get()};
+        }
+        double v[1][kIPT];
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) v[0][j] = acc[j].get();
         if (!breduce<1>(v, a.partial, parity, S, sh, BS, a.bar, err)) return;
       }
       if (threadIdx.x < BS) {
@@ -338,18 +454,22 @@ pcg_batched_persistent(BatchArgs a) {
       __syncthreads();
       if (S.count == 0) break;
       // preconditioner on the iterating instances
-      for (int64_t i = row0; i < n; i += rstep)
-        if (S.iterating[b]) a.t[i * BS + b] = fsai_row(a, i, b, true, a.r);
+      if (any4(S.iterating))
+        for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4(a, i, q, true, R);
       if (!bgrid_sync(a.bar, err)) return;
       {
-        Acc2 rz;
-        for (int64_t i = row0; i < n; i += rstep)
-          if (S.iterating[b]) {
-            const float zi = fsai_row(a, i, b, false, a.t);
-            a.z[i * BS + b] = zi;
-            rz.add(a.r[i * BS + b], zi);
+        Acc2 acc[kIPT];
+        if (any4(S.iterating))
+          for (int64_t i = row0; i < n; i += rstep) {
+            const float4 zi = fsai4(a, i, q, false, T);
+            Z[i * TPR + q] = zi;
+            const float4 ri = R[i * TPR + q];
+#pragma unroll
+            for (int j = 0; j < kIPT; ++j) acc[j].add(get4(ri, j), get4(zi, j));
           }
-        double v[1] = {rz.get()};
+        double v[1][kIPT];
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) v[0][j] = acc[j].get();
         if (!breduce<1>(v, a.partial, parity, S, sh, BS, a.bar, err)) return;
       }
       if (threadIdx.x < BS) {
@@ -360,29 +480,53 @@ pcg_batched_persistent(BatchArgs a) {
         }
       }
       __syncthreads();
-      for (int64_t e = e0; e < ne; e += estep)
-        if (S.iterating[b]) a.p[e] = fmaf(S.beta[b], a.p[e], a.z[e]);
+      if (any4(S.iterating)) {
+        float4 bt;
+        bool on[kIPT];
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) {
+          set4(bt, j, S.beta[kIPT * q + j]);
+          on[j] = act(S.iterating, j);
+        }
+        for (int64_t e = e0; e < nq; e += estep) {
+          const float4 zv = Z[e];
+          float4 pv = Pv[e];
+          if (on[0]) pv.x = fmaf(bt.x, pv.x, zv.x);
+          if (on[1]) pv.y = fmaf(bt.y, pv.y, zv.y);
+          if (on[2]) pv.z = fmaf(bt.z, pv.z, zv.z);
+          if (on[3]) pv.w = fmaf(bt.w, pv.w, zv.w);
+          Pv[e] = pv;
+        }
+      }
       if (!bgrid_sync(a.bar, err)) return;
     }
 
     // ---- reliable update of the active instances
-    for (int64_t e = e0; e < ne; e += estep)
-      if (S.active[b]) {
-        a.x64[e] += (double)a.x[e];
-        a.x[e] = 0.0f;
+    if (any4(S.active))
+      for (int64_t e = e0; e < nq; e += estep) {
+        const float4 xv = X[e];
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) a.x64[e * kIPT + j] += (double)get4(xv, j);
+        X[e] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     if (!bgrid_sync(a.bar, err)) return;
     {
-      double rr = 0.0;
-      for (int64_t i = row0; i < n; i += rstep)
-        if (S.active[b]) {
-          const int64_t e = i * BS + b;
-          const double ri = a.bvec[e] - edge_form_row<double>(a, i, b, state, a.x64, a.w64);
-          a.r64[e] = ri;
-          a.r[e] = (float)ri;
-          rr = fma(ri, ri, rr);
+      double v[1][kIPT] = {{0.0, 0.0, 0.0, 0.0}};
+      if (any4(S.active))
+        for (int64_t i = row0; i < n; i += rstep) {
+          double y[kIPT];
+          edge_form4_64(a, i, q, st, a.x64, y);
+          float4 rf;
+#pragma unroll
+          for (int j = 0; j < kIPT; ++j) {
+            const int64_t e = i * BS + kIPT * q + j;
+            const double ri = a.bvec[e] - y[j];
+            a.r64[e] = ri;
+            set4(rf, j, (float)ri);
+            v[0][j] = fma(ri, ri, v[0][j]);
+          }
+          R[i * TPR + q] = rf;
         }
-      double v[1] = {rr};
       if (!breduce<1>(v, a.partial, parity, S, sh, BS, a.bar, err)) return;
     }
     if (threadIdx.x < BS) {

@@ -1,7 +1,9 @@
 // dec_hodge.cu - the diagonal Hodge star *1 on primal edges from the
-// circumcentric dual (Sec. 2.1: ratio of dual to primal volumes), with the
-// conductivity of each tet scaling its share (Sec. 2.1) and penny cracks
-// making cut dual faces insulating (Sec. 2.5).
+// circumcentric dual (Sec. 2.1: ratio of dual to primal volumes), times the
+// conductivity of the dual face (Sec. 2.1), with penny cracks making cut dual
+// faces insulating (Sec. 2.5).  A per-tet conductivity k_T is carried onto
+// the dual face of e as the mean of k_T over the tets around e, weighted by
+// the unsigned areas of their parts of the face.
 //
 // One thread per tet computes, in FP64, for each of its 6 edges the signed
 // area of the dual-face piece inside the tet divided by the edge length.
@@ -17,7 +19,8 @@
 // division and square root are expensive on GB300).  The crack test runs on
 // the sub-triangles themselves, with face circumcentres computed only when
 // discs are present.  A second pass sums the
-// pieces of every edge in a fixed order (sorted tet*6+slot), so *1 is
+// pieces of every edge (and, with a conductivity field, the k-weighted and
+// plain unsigned part areas) in a fixed order (sorted tet*6+slot), so *1 is
 // deterministic without atomics.
 #include "dec_internal.cuh"
 
@@ -98,6 +101,7 @@ struct DiscGrid {
   const double* scales;   // [n_states]
   int n_states;
   int nd;
+  double smax;            // largest radius scale
 };
 
 __constant__ int kEdgeA[6] = {0, 0, 0, 1, 1, 2};
@@ -108,8 +112,8 @@ __constant__ int kEdgeD[6] = {3, 3, 2, 3, 2, 1};
 __global__ void __launch_bounds__(128)
 hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
                  const double* __restrict__ kcond, int64_t m,
-                 double* __restrict__ piece, uint8_t* __restrict__ slot_cut,
-                 DiscGrid grid) {
+                 double* __restrict__ piece, double* __restrict__ kpart,
+                 uint8_t* __restrict__ slot_cut, DiscGrid grid) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
        t += (int64_t)gridDim.x * blockDim.x) {
     int4 v4 = reinterpret_cast<const int4*>(tets)[t];
@@ -120,6 +124,7 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
       X[i] = mk(xyz[3 * (int64_t)vid[i]], xyz[3 * (int64_t)vid[i] + 1],
                 xyz[3 * (int64_t)vid[i] + 2]);
     const double kT = kcond ? kcond[t] : 1.0;
+    const int64_t q6 = 6 * m;
     // all vectors relative to X[0]
     V3 R[4];
     R[0] = mk(0.0, 0.0, 0.0);
@@ -151,7 +156,13 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
       const int ea = kEdgeA[s], eb = kEdgeB[s], ec = kEdgeC[s], ed = kEdgeD[s];
       const double cot_c = dot(R[ea] - R[ec], R[eb] - R[ec]);   // face opposite d
       const double cot_d = dot(R[ea] - R[ed], R[eb] - R[ed]);   // face opposite c
-      piece[t * 6 + s] = kT * 0.25 * (cot_c * H[ed] + cot_d * H[ec]);
+      const double a0 = 0.25 * cot_c * H[ed], a1 = 0.25 * cot_d * H[ec];
+      piece[t * 6 + s] = a0 + a1;
+      if (kcond) {                       // unsigned part of the face, with and without k
+        const double u = fabs(a0) + fabs(a1);
+        kpart[t * 6 + s] = kT * u;
+        kpart[q6 + t * 6 + s] = u;
+      }
       first[s] = (uint8_t)grid.n_states;
     }
     if (grid.nd > 0) {
@@ -180,11 +191,26 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
         c0[d] = (int)fmax(0.0, floor(f0));
         c1[d] = (int)fmin((double)grid.dim[d] - 1.0, floor(f1));
       }
+      // Every dual sub-triangle of the tet lies in its circumball (c_T is
+      // the centre; m_e and c_F are projections of c_T onto an edge line and
+      // a face plane), so a disc that misses the ball cuts none of them.
+      // The test is conservative (the in-plane reach is bounded by r + R_T)
+      // with a relative margin; the cut decision itself stays exact.
+      const double RT2 = dot(cT, cT) * (1.0 + 1e-9) + 1e-300;
+      const double RT = sqrt(RT2);
       auto test_disc = [&](int id) {
         const double* dsc = grid.discs + 7 * (int64_t)id;
         V3 dc = mk(dsc[0], dsc[1], dsc[2]);
         V3 dn = mk(dsc[3], dsc[4], dsc[5]);
         const double r = dsc[6];
+        {
+          const V3 v = cTa - dc;
+          const double dp = dot(v, dn);
+          if (dp * dp > RT2) return;                      // ball misses the plane
+          const double par2 = dot(v, v) - dp * dp;
+          const double reach = grid.smax * r * (1.0 + 1e-9);
+          if (par2 > reach * reach + 2.0 * reach * RT + RT2) return;
+        }
 #pragma unroll
         for (int s = 0; s < 6; ++s) {
           if (first[s] == 0) continue;
@@ -224,22 +250,30 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
 }
 
 // *1[e] = sum of the pieces of e (already divided by |e|), in increasing
-// tet*6+slot order; first_cut[e] = min over those slots.
+// tet*6+slot order, times kappa_e = sum k_T u_T / sum u_T (u_T the unsigned
+// part areas, kpart = [k u | u], absent for k = 1); first_cut[e] = min over
+// those slots.
 __global__ void edge_reduce_kernel(const int32_t* __restrict__ seg_start,
                                    const uint32_t* __restrict__ seg_pay,
                                    const double* __restrict__ piece,
+                                   const double* __restrict__ kpart, int64_t q6,
                                    const uint8_t* __restrict__ slot_cut,
                                    int64_t ne, double* __restrict__ w,
                                    uint8_t* __restrict__ first_cut) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double sum = 0.0;
+    double sum = 0.0, ku = 0.0, u = 0.0;
     unsigned fc = 255u;
     for (int32_t k = seg_start[e]; k < seg_start[e + 1]; ++k) {
       uint32_t p = seg_pay[k];
       sum += piece[p];
+      if (kpart) {
+        ku += kpart[p];
+        u += kpart[q6 + p];
+      }
       fc = min(fc, (unsigned)slot_cut[p]);
     }
+    if (kpart) sum = u > 0.0 ? sum * (ku / u) : 0.0;
     w[e] = sum;
     first_cut[e] = (uint8_t)fc;
   }
@@ -302,7 +336,7 @@ dec_status validate_k(dec_ctx* ctx) {
 dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k) {
   cudaStream_t s = ctx->stream;
   const int64_t m = ctx->m, q = 6 * m;
-  DEC_TRY(ctx->piece.ensure(q));
+  DEC_TRY(ctx->piece.ensure(has_k ? 3 * q : q));   // [piece | k u | u]
   DEC_TRY(ctx->slot_cut.ensure(q));
   DEC_TRY(ctx->w.ensure(ctx->ne));
   DEC_TRY(ctx->first_cut.ensure(ctx->ne));
@@ -320,6 +354,7 @@ dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k) {
                             cudaMemcpyDeviceToHost, s));
     DEC_TRY(cudaStreamSynchronize(s));
     const double smax = hs.back();
+    g.smax = smax;
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, rmax = 0;
     for (int64_t i = 0; i < nd; ++i) {
       const double R = hd[7 * i + 6] * smax;
@@ -365,12 +400,13 @@ dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k) {
   if (blocks > (int64_t)ctx->num_sms * 64) blocks = (int64_t)ctx->num_sms * 64;
   hodge_tet_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 128, 0, s>>>(
       ctx->xyz.p, ctx->tets.p, has_k ? ctx->kcond.p : nullptr,
-      m, ctx->piece.p, ctx->slot_cut.p, g);
+      m, ctx->piece.p, has_k ? ctx->piece.p + q : nullptr, ctx->slot_cut.p, g);
   DEC_TRY(cudaGetLastError());
   int64_t eb = (ctx->ne + 255) / 256;
   if (eb > (int64_t)ctx->num_sms * 32) eb = (int64_t)ctx->num_sms * 32;
   edge_reduce_kernel<<<(unsigned)std::max<int64_t>(eb, 1), 256, 0, s>>>(
-      ctx->seg_start.p, ctx->seg_pay.p, ctx->piece.p, ctx->slot_cut.p, ctx->ne,
+      ctx->seg_start.p, ctx->seg_pay.p, ctx->piece.p, has_k ? ctx->piece.p + q : nullptr, q,
+      ctx->slot_cut.p, ctx->ne,
       ctx->w.p, ctx->first_cut.p);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 2;

@@ -288,7 +288,7 @@ def test_device_resident_inputs(abi, ctx):
 
 def test_batched_crack_states_match_oracle(abi, ctx):
     """All crack states of a growing disc population in one batched launch
-    (shared FSAI factor of the uncracked operator, per-instance masks)."""
+    (one FSAI factor per state, per-instance masks)."""
     wl = make_workload("growth96", N=10, n_discs=8, n_scales=6)
     ref = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k,
                        discs=wl.discs, scales=wl.scales, precond="fsai",
