@@ -305,7 +305,7 @@ def gpu_arm(args, rank, world):
             "spmv_f32": round(bytes32 / (spmv32_ms * 1e-3) / 1e9, 1),
             "fsai_apply_f64": round(fsai_bytes64 / (fsai_ms * 1e-3) / 1e9, 1) if fsai_ms else None,
             "fsai_apply_bf16": round(fsai_bytes16 / (fsai16_ms * 1e-3) / 1e9, 1) if fsai16_ms else None},
-        "roofline": {"kernel": "spmv_pq_kernel<8,double,double> (CSR SpMV + p.q)",
+        "roofline": {"kernel": "spmv_pq_kernel<double,double> (SELL-32 SpMV + p.q, FP64)",
                      "bound": "hbm", "achieved": round(gbs, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
                      "peak_kind": f"{peak_kind} burst copy",
