@@ -86,7 +86,9 @@ enum {
                           FP32 residual replaced by r = b - L x in FP64 each
                           time it has dropped by 1e-2, keeping the search
                           direction; convergence is decided in FP64.  Runs
-                          as one persistent cooperative kernel per instance */
+                          as one persistent cooperative kernel per instance
+                          up to 400,000 nodes, as one kernel per phase
+                          above                                            */
   DEC_MODE_MIXED_PHASED = 2, /* the same solve as DEC_MODE_MIXED, run as one
                                 kernel per phase (CUDA graphs) instead    */
   DEC_MODE_MIXED_BATCHED = 3  /* the mixed solve of all instances (crack

@@ -79,9 +79,10 @@ dec_status dec_create(dec_ctx** out, int device, void* stream) {
   }
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) {
-    ctx->reduce_grid = ctx->num_sms * 4;
+    ctx->reduce_grid = ctx->num_sms * 8;   // the most blocks a reducing kernel runs
     e = ctx->partial.ensure((size_t)dec::kRedSlots * ctx->reduce_grid);
   }
+  if (e == cudaSuccess) e = dec::init_kernel_attributes();
   if (e == cudaSuccess) e = ctx->ticket.ensure(1);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ticket.p, 0, sizeof(unsigned), ctx->stream);
   if (e == cudaSuccess) e = ctx->cg.ensure(1);
@@ -137,7 +138,7 @@ dec_status dec_mesh_upload(dec_ctx* ctx, const double* xyz, int64_t n_nodes,
       1, std::min<int64_t>((n_nodes + dec::kBlock - 1) / dec::kBlock, (int64_t)ctx->num_sms * 2));
   ctx->grid_sell = (int)std::max<int64_t>(
       1, std::min<int64_t>((ctx->sellL.nslices + 7) / 8, (int64_t)ctx->num_sms * 4));
-  ctx->reduce_grid = std::max(ctx->grid_vec, ctx->grid_sell);
+  ctx->reduce_grid = std::max(std::max(ctx->grid_vec, ctx->grid_sell), ctx->num_sms * 8);
   DEC_TRY(ctx->partial.ensure((size_t)dec::kRedSlots * ctx->reduce_grid));
   DEC_TRY(cudaStreamSynchronize(s));
   ctx->stage = 1;

@@ -329,4 +329,6 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
                          double* relres);
 dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
                        double* avg_ms);
+// shared-memory limits of the staged SELL kernels (current device)
+cudaError_t init_kernel_attributes();
 }  // namespace dec

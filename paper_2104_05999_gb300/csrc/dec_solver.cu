@@ -53,24 +53,87 @@ cg_init_kernel(int64_t n, const BT* __restrict__ b, VT* __restrict__ x,
   }
 }
 
+// Widths (entries per row) staged in shared memory by the SELL kernels.
+// The FSAI halves (at most 14 entries per row on the Delaunay meshes here)
+// are staged: their BF16 apply ran 1.3-1.5x faster than with register
+// chunks.  L (16 per row on average, 26 at most) keeps register chunks
+// (kStageL = 0): staging its wider slices cut the resident warps and ran
+// slower, in FP64 and in FP32.
+#ifndef DEC_STAGE_L
+#define DEC_STAGE_L 0
+#endif
+#ifndef DEC_STAGE_G
+#define DEC_STAGE_G 14
+#endif
+// entries per register chunk of L's row product (unstaged)
+#ifndef DEC_CHUNK_L
+#define DEC_CHUNK_L 8
+#endif
+// resident blocks per SM the unstaged SELL kernels are sized for
+#ifndef DEC_SELL_PER_SM
+#define DEC_SELL_PER_SM 4
+#endif
+constexpr int kStageL = DEC_STAGE_L;
+constexpr int kStageG = DEC_STAGE_G;
+constexpr int kChunkL = DEC_CHUNK_L;
+// The mixed mode runs as one persistent kernel up to this many nodes (its
+// 3 grid barriers per iteration beat 5 launches when the matrices sit in
+// L2) and as per-phase kernels above (more warps in flight per SM: 1.5x
+// faster per iteration at 128^3).
+constexpr int64_t kPersistMaxRows = 400000;
+
+// Dynamic shared memory of a SELL kernel block and the number of its blocks:
+// one slice per warp, at most 4 resident blocks per SM (the reduction
+// partials are sized for 4 * SMs blocks), fewer when the stage is large.
+template <int WMAX, typename MT>
+constexpr int sell_smem() {
+  return WMAX ? (kBlock / 32) * stage_bytes<WMAX, MT>() : 0;
+}
+template <int WMAX, typename MT>
+static unsigned sell_grid(const dec_ctx* ctx, int64_t nslices) {
+  constexpr int smem = sell_smem<WMAX, MT>();
+  const int per_sm = smem ? std::max(1, std::min(4, (200 * 1024) / smem)) : DEC_SELL_PER_SM;
+  return (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((nslices + kBlock / 32 - 1) / (kBlock / 32),
+                           (int64_t)ctx->num_sms * per_sm));
+}
+
+// the warp's shared-memory stage (WMAX > 0) or nullptr
+template <int WMAX, typename MT>
+__device__ __forceinline__ unsigned char* warp_stage() {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  if constexpr (WMAX > 0) return dsm + (threadIdx.x >> 5) * stage_bytes<WMAX, MT>();
+  else return nullptr;
+}
+
+// body(row, (A x)_row) over every row, one slice per warp at a time
+template <int WMAX, int CHUNK, typename MT, typename VT, typename Body>
+__device__ __forceinline__ void for_rows(const SellArg<MT>& A, const VT* __restrict__ x,
+                                         Body&& body) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (kBlock / 32);
+  const int64_t first = blockIdx.x * (int64_t)(kBlock / 32) + (threadIdx.x >> 5);
+  unsigned char* st = warp_stage<WMAX, MT>();
+  for (int64_t s = first; s < A.nslices; s += warps) {
+    const int32_t r = __ldg(A.perm + 32 * s + lane);
+    VT acc;
+    if constexpr (WMAX > 0) acc = sell_row_staged<WMAX>(A, s, lane, x, st);
+    else acc = sell_row<MT, VT, CHUNK>(A, s, lane, x);
+    if (r >= 0) body(r, acc);
+  }
+}
+
 // q = A p and alpha = (r.z) / (p.q)
-template <typename MT, typename VT>
+template <int WMAX, typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock)
 spmv_pq_kernel(SellArg<MT> A, const VT* __restrict__ p, VT* __restrict__ q,
                CgScalars* cg, double* partial, unsigned* ticket) {
   if (*(volatile int*)&cg->done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (kBlock / 32);
   double pq = 0.0;
-  for (int64_t s = blockIdx.x * (int64_t)(kBlock / 32) + (threadIdx.x >> 5);
-       s < A.nslices; s += warps) {
-    const int32_t r = __ldg(A.perm + 32 * s + lane);
-    const VT acc = sell_row(A, s, lane, p);
-    if (r >= 0) {
-      q[r] = acc;
-      pq += to_d(p[r]) * to_d(acc);
-    }
-  }
+  for_rows<WMAX, kChunkL>(A, p, [&](int32_t r, VT acc) {
+    q[r] = acc;
+    pq += to_d(p[r]) * to_d(acc);
+  });
   double v[1] = {pq}, t[1];
   if (grid_reduce<kBlock, 1>(v, t, partial, ticket) && threadIdx.x == 0) {
     const double den = t[0];
@@ -143,41 +206,27 @@ update_kernel(int64_t n, VT* __restrict__ x, VT* __restrict__ r,
 }
 
 // y = A x (FSAI first half: t = G r)
-template <typename MT, typename VT>
+template <int WMAX, typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock)
 sell_apply_kernel(SellArg<MT> A, const VT* __restrict__ x, VT* __restrict__ y,
                   const CgScalars* cg) {
   if (*(volatile const int*)&cg->done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (kBlock / 32);
-  for (int64_t s = blockIdx.x * (int64_t)(kBlock / 32) + (threadIdx.x >> 5);
-       s < A.nslices; s += warps) {
-    const int32_t r = __ldg(A.perm + 32 * s + lane);
-    const VT acc = sell_row(A, s, lane, x);
-    if (r >= 0) y[r] = acc;
-  }
+  for_rows<WMAX, 8>(A, x, [&](int32_t r, VT acc) { y[r] = acc; });
 }
 
 // z = A t (FSAI second half: z = G^T t), r.z, then beta = (r.z)_new /
 // (r.z)_old.  `init` keeps beta = 0.
-template <typename MT, typename VT>
+template <int WMAX, typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock)
 sell_apply_dot_kernel(SellArg<MT> A, const VT* __restrict__ t,
                       const VT* __restrict__ r, VT* __restrict__ z, int init,
                       CgScalars* cg, double* partial, unsigned* ticket) {
   if (*(volatile int*)&cg->done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (kBlock / 32);
   double rz = 0.0;
-  for (int64_t s = blockIdx.x * (int64_t)(kBlock / 32) + (threadIdx.x >> 5);
-       s < A.nslices; s += warps) {
-    const int32_t row = __ldg(A.perm + 32 * s + lane);
-    const VT acc = sell_row(A, s, lane, t);
-    if (row >= 0) {
-      z[row] = acc;
-      rz += to_d(r[row]) * to_d(acc);
-    }
-  }
+  for_rows<WMAX, 8>(A, t, [&](int32_t row, VT acc) {
+    z[row] = acc;
+    rz += to_d(r[row]) * to_d(acc);
+  });
   double v[1] = {rz}, tt[1];
   if (grid_reduce<kBlock, 1>(v, tt, partial, ticket) && threadIdx.x == 0) {
     cg->beta = init ? 0.0 : tt[0] / cg->rz;
@@ -317,6 +366,25 @@ k_eff_kernel(int64_t n, const int32_t* __restrict__ rowptr,
   }
 }
 
+// Opt every staged SELL kernel into its dynamic shared memory (the FP64
+// stage of L is above the 48 KB default).
+cudaError_t init_kernel_attributes() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f, int bytes) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  };
+  set((const void*)spmv_pq_kernel<kStageL, double, double>, sell_smem<kStageL, double>());
+  set((const void*)spmv_pq_kernel<kStageL, float, float>, sell_smem<kStageL, float>());
+  set((const void*)sell_apply_kernel<kStageG, double, double>, sell_smem<kStageG, double>());
+  set((const void*)sell_apply_dot_kernel<kStageG, double, double>, sell_smem<kStageG, double>());
+  set((const void*)sell_apply_kernel<kStageG, __nv_bfloat16, float>,
+      sell_smem<kStageG, __nv_bfloat16>());
+  set((const void*)sell_apply_dot_kernel<kStageG, __nv_bfloat16, float>,
+      sell_smem<kStageG, __nv_bfloat16>());
+  return e;
+}
+
 // ------------------------------------------------------------- driver
 constexpr int kChunk = 16;       // iterations per graph launch / host poll
 
@@ -333,22 +401,27 @@ static void launch_iterations(dec_ctx* ctx, int64_t n, const Ops<MT, PT, DT>& op
                               VT* x, VT* r, VT* z, VT* p, VT* q, VT* t, int max_iter,
                               int count) {
   cudaStream_t s = ctx->stream;
-  const unsigned G = (unsigned)ctx->grid_vec, Gs = (unsigned)ctx->grid_sell;
+  const unsigned G = (unsigned)ctx->grid_vec;
+  const unsigned GA = sell_grid<kStageL, MT>(ctx, op.A.nslices);
+  const unsigned GL = sell_grid<kStageG, PT>(ctx, op.Glo.nslices);
+  const unsigned GU = sell_grid<kStageG, PT>(ctx, op.Gup.nslices);
+  constexpr int SA = sell_smem<kStageL, MT>(), SG = sell_smem<kStageG, PT>();
   CgScalars* cg = ctx->cg.p;
   double* part = ctx->partial.p;
   unsigned* tk = ctx->ticket.p;
   const bool jac = ctx->precond == DEC_PRECOND_JACOBI;
   ctx->launches += (int64_t)count * (jac ? 3 : 5);
   for (int it = 0; it < count; ++it) {
-    spmv_pq_kernel<MT, VT><<<Gs, kBlock, 0, s>>>(op.A, p, q, cg, part, tk);
+    spmv_pq_kernel<kStageL, MT, VT><<<GA, kBlock, SA, s>>>(op.A, p, q, cg, part, tk);
     if (jac) {
       update_kernel<VT, DT, true><<<G, kBlock, 0, s>>>(n, x, r, p, q, op.dinv, z,
                                                        max_iter, cg, part, tk);
     } else {
       update_kernel<VT, DT, false><<<G, kBlock, 0, s>>>(n, x, r, p, q, op.dinv, z,
                                                         max_iter, cg, part, tk);
-      sell_apply_kernel<PT, VT><<<Gs, kBlock, 0, s>>>(op.Glo, r, t, cg);
-      sell_apply_dot_kernel<PT, VT><<<Gs, kBlock, 0, s>>>(op.Gup, t, r, z, 0, cg, part, tk);
+      sell_apply_kernel<kStageG, PT, VT><<<GL, kBlock, SG, s>>>(op.Glo, r, t, cg);
+      sell_apply_dot_kernel<kStageG, PT, VT><<<GU, kBlock, SG, s>>>(op.Gup, t, r, z, 0, cg,
+                                                                    part, tk);
     }
     xpay_kernel<VT><<<G, kBlock, 0, s>>>(n, z, p, cg);
   }
@@ -361,16 +434,19 @@ template <typename VT, typename MT, typename PT, typename DT>
 static void launch_restart(dec_ctx* ctx, int64_t n, const Ops<MT, PT, DT>& op, VT* r,
                            VT* z, VT* p, VT* t, int init = 1) {
   cudaStream_t s = ctx->stream;
-  const unsigned G = (unsigned)ctx->grid_vec, Gs = (unsigned)ctx->grid_sell;
+  const unsigned G = (unsigned)ctx->grid_vec;
+  constexpr int SG = sell_smem<kStageG, PT>();
   CgScalars* cg = ctx->cg.p;
   ctx->launches += ctx->precond == DEC_PRECOND_JACOBI ? 2 : 3;
   if (ctx->precond == DEC_PRECOND_JACOBI) {
     jacobi_init_kernel<VT, DT><<<G, kBlock, 0, s>>>(n, op.dinv, r, z, init, cg,
                                                     ctx->partial.p, ctx->ticket.p);
   } else {
-    sell_apply_kernel<PT, VT><<<Gs, kBlock, 0, s>>>(op.Glo, r, t, cg);
-    sell_apply_dot_kernel<PT, VT><<<Gs, kBlock, 0, s>>>(op.Gup, t, r, z, init, cg,
-                                                       ctx->partial.p, ctx->ticket.p);
+    sell_apply_kernel<kStageG, PT, VT><<<sell_grid<kStageG, PT>(ctx, op.Glo.nslices), kBlock,
+                                         SG, s>>>(op.Glo, r, t, cg);
+    sell_apply_dot_kernel<kStageG, PT, VT><<<sell_grid<kStageG, PT>(ctx, op.Gup.nslices),
+                                             kBlock, SG, s>>>(op.Gup, t, r, z, init, cg,
+                                                              ctx->partial.p, ctx->ticket.p);
   }
   xpay_kernel<VT><<<G, kBlock, 0, s>>>(n, z, p, cg);
 }
@@ -462,7 +538,7 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
       DEC_TRY(cudaGetLastError());
     }
     DEC_TRY(cudaMemcpyAsync(u, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  } else if (mode == DEC_MODE_MIXED &&
+  } else if (mode == DEC_MODE_MIXED && n <= kPersistMaxRows &&
              (st = solve_mixed_persistent(ctx, inst, rtol, max_iter, iters_out, relres_out)) !=
                  DEC_ERR_LIMIT) {
     return st;   // the whole mixed solve ran as one cooperative kernel
@@ -565,7 +641,6 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
                        double* avg_ms) {
   const int64_t n = ctx->n;
   cudaStream_t s = ctx->stream;
-  const unsigned G = (unsigned)ctx->grid_sell;
   DEC_TRY(ctx->flush.ensure(flush_bytes > 0 ? flush_bytes : 1));
   for (auto* bf : {&ctx->p64, &ctx->q64, &ctx->t64, &ctx->z64, &ctx->r64}) DEC_TRY(bf->ensure(n));
   for (auto* bf : {&ctx->p32, &ctx->q32, &ctx->t32, &ctx->z32, &ctx->r32}) DEC_TRY(bf->ensure(n));
@@ -594,28 +669,36 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
     DEC_TRY(cudaEventRecord(e0, s));
     switch (which) {
       case DEC_KERNEL_SPMV_F64:
-        spmv_pq_kernel<double, double><<<G, kBlock, 0, s>>>(L64, ctx->p64.p, ctx->q64.p,
-                                                            ctx->cg.p, ctx->partial.p,
-                                                            ctx->ticket.p);
+        spmv_pq_kernel<kStageL, double, double>
+            <<<sell_grid<kStageL, double>(ctx, L64.nslices), kBlock,
+               sell_smem<kStageL, double>(), s>>>(L64, ctx->p64.p, ctx->q64.p, ctx->cg.p,
+                                                  ctx->partial.p, ctx->ticket.p);
         break;
       case DEC_KERNEL_SPMV_F32:
-        spmv_pq_kernel<float, float><<<G, kBlock, 0, s>>>(L32, ctx->p32.p, ctx->q32.p,
-                                                          ctx->cg.p, ctx->partial.p,
-                                                          ctx->ticket.p);
+        spmv_pq_kernel<kStageL, float, float>
+            <<<sell_grid<kStageL, float>(ctx, L32.nslices), kBlock,
+               sell_smem<kStageL, float>(), s>>>(L32, ctx->p32.p, ctx->q32.p, ctx->cg.p,
+                                                 ctx->partial.p, ctx->ticket.p);
         break;
       case DEC_KERNEL_FSAI_F64:
-        sell_apply_kernel<double, double><<<G, kBlock, 0, s>>>(Glo64, ctx->r64.p, ctx->t64.p,
-                                                               ctx->cg.p);
-        sell_apply_dot_kernel<double, double><<<G, kBlock, 0, s>>>(
-            Gup64, ctx->t64.p, ctx->r64.p, ctx->z64.p, 1, ctx->cg.p, ctx->partial.p,
-            ctx->ticket.p);
+        sell_apply_kernel<kStageG, double, double>
+            <<<sell_grid<kStageG, double>(ctx, Glo64.nslices), kBlock,
+               sell_smem<kStageG, double>(), s>>>(Glo64, ctx->r64.p, ctx->t64.p, ctx->cg.p);
+        sell_apply_dot_kernel<kStageG, double, double>
+            <<<sell_grid<kStageG, double>(ctx, Gup64.nslices), kBlock,
+               sell_smem<kStageG, double>(), s>>>(Gup64, ctx->t64.p, ctx->r64.p, ctx->z64.p,
+                                                  1, ctx->cg.p, ctx->partial.p, ctx->ticket.p);
         break;
       case DEC_KERNEL_FSAI_BF16:
-        sell_apply_kernel<__nv_bfloat16, float><<<G, kBlock, 0, s>>>(
-            Glo16, ctx->r32.p, ctx->t32.p, ctx->cg.p);
-        sell_apply_dot_kernel<__nv_bfloat16, float><<<G, kBlock, 0, s>>>(
-            Gup16, ctx->t32.p, ctx->r32.p, ctx->z32.p, 1, ctx->cg.p, ctx->partial.p,
-            ctx->ticket.p);
+        sell_apply_kernel<kStageG, __nv_bfloat16, float>
+            <<<sell_grid<kStageG, __nv_bfloat16>(ctx, Glo16.nslices), kBlock,
+               sell_smem<kStageG, __nv_bfloat16>(), s>>>(Glo16, ctx->r32.p, ctx->t32.p,
+                                                         ctx->cg.p);
+        sell_apply_dot_kernel<kStageG, __nv_bfloat16, float>
+            <<<sell_grid<kStageG, __nv_bfloat16>(ctx, Gup16.nslices), kBlock,
+               sell_smem<kStageG, __nv_bfloat16>(), s>>>(Gup16, ctx->t32.p, ctx->r32.p,
+                                                         ctx->z32.p, 1, ctx->cg.p,
+                                                         ctx->partial.p, ctx->ticket.p);
         break;
       default:
         st = ctx->fail(DEC_ERR_ARG, "time_kernel: unknown kernel id");
