@@ -36,6 +36,26 @@ METRIC = "PCG time to rel-res 1e-10 & SpMV HBM GB/s: mixed/batched vs FP64, 1 GB
 L2_FLUSH = 512 << 20
 
 
+def sync_ranks(world, device):
+    """Device synchronize, then a barrier across ranks: brackets the timed
+    region on both sides."""
+    import torch
+    if device is not None and torch.device(device).type == "cuda":
+        torch.cuda.synchronize(device)
+    if world > 1:
+        torch.distributed.barrier()
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _log(msg):
     print(f"[bench] {msg}", file=sys.stderr, flush=True)
 
@@ -163,12 +183,14 @@ def gpu_arm(args, rank, world):
         del src
         return iters, relres, q_in
 
-    def timed(mode, steps, warmup, host=False):
+    def timed(mode, steps, warmup, host=False, bracket=False):
         T_out = None
         if host:
             T_out = torch.empty((wl.batch, wl.n), dtype=torch.float64).pin_memory()
         for _ in range(warmup):
             step(mode, host, T_out)
+        if bracket:
+            sync_ranks(world, dev)
         times = []
         launches0 = ctx.dec_get_launch_count()
         res = None
@@ -184,21 +206,16 @@ def gpu_arm(args, rank, world):
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         launches = (ctx.dec_get_launch_count() - launches0) / max(steps, 1)
+        if bracket:
+            sync_ranks(world, dev)
         return times, res, launches
 
 
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(dev_id) as clk:
-        times, (iters, relres, q_in), launches = timed(mode64, args.steps, args.warmup)
+        times, (iters, relres, q_in), launches = timed(mode64, args.steps, args.warmup,
+                                                       bracket=True)
     _log(f"timed steps: {[round(t, 3) for t in times]} ms")
-    torch.cuda.synchronize()
-    ms = statistics.mean(times)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(statistics.mean(times), world, dev)
 
     # the other precision on the same inputs (comparison, fewer steps)
     o_times, (o_iters, o_relres, o_q), _ = timed(other, max(2, args.steps // 2), 1)
@@ -261,14 +278,36 @@ def gpu_arm(args, rank, world):
     fsai_bytes64 = 2 * (12 * nnz_g + 4 * (n + 1) + 16 * n) + 8 * n
     fsai_bytes16 = 2 * (6 * nnz_g + 4 * (n + 1) + 8 * n) + 4 * n
     peak, peak_kind = _peaks()
-    gbs = bytes64 / (spmv_ms * 1e-3) / 1e9
+    solve_ms = statistics.mean(s_times)
+    # the dominant kernel of the timed mode: the FP64 SpMV (FP64 mode), the
+    # FP32 SpMV (mixed modes) or the batched persistent PCG, whose figure is
+    # per iteration: algorithmic bytes of one iteration over the solve time
+    # per iteration of the slowest instance
+    roof_kernel = "spmv_pq_kernel<double,double> (SELL-32 SpMV + p.q, FP64)"
+    roof_bytes, roof_ms = bytes64, spmv_ms
+    if want in ("mixed", "mixed_phased"):
+        roof_kernel = "spmv_pq_kernel<float,float> (SELL-32 SpMV + p.q, FP32)"
+        roof_bytes, roof_ms = bytes32, spmv32_ms
+    elif want == "batched":
+        BS = 8
+        while BS < B:
+            BS *= 2
+        per_inst_g = wl.scales is not None and len(wl.scales) > 1
+        vec = 4 * n * BS
+        roof_bytes = (9 * nnz + 2 * nnz_g * (4 + 2 * (BS if per_inst_g else 1)) +
+                      vec * (2 + 2 + 2 + 9))
+        roof_ms = solve_ms / max(1, int(np.max(iters)))
+        roof_kernel = ("pcg_batched_persistent (per FP32 iteration: edge-form SpMM "
+                       "over %d instances + both FSAI halves + vector updates)" % B)
+    roof_gbs = roof_bytes / (roof_ms * 1e-3) / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "spmv_f64_traffic.json")
     if os.path.exists(tpath):
         try:
             with open(tpath) as f:
                 tj = json.load(f)
-            if tj.get("workload") == wl.name and tj.get("kernel_rev") == KERNEL_REV:
+            if (tj.get("workload") == wl.name and tj.get("kernel_rev") == KERNEL_REV
+                    and want == "fp64"):
                 traffic = tj["bytes_per_launch"]
         except Exception:
             traffic = None
@@ -290,7 +329,7 @@ def gpu_arm(args, rank, world):
         "k_eff": float(q_in[0]),
         "iters_per_instance": [int(v) for v in iters] if len(iters) > 1 else None,
         "k_eff_per_instance": [float(v) for v in q_in] if len(q_in) > 1 else None,
-        "solve_ms": round(statistics.mean(s_times), 4),
+        "solve_ms": round(solve_ms, 4),
         "phases_ms": phases,
         "other_mode": {"mode": "mixed" if other == abi.DEC_MODE_MIXED else "fp64 per instance",
                        "ms_per_step": round(statistics.mean(o_times), 4),
@@ -305,12 +344,13 @@ def gpu_arm(args, rank, world):
             "spmv_f32": round(bytes32 / (spmv32_ms * 1e-3) / 1e9, 1),
             "fsai_apply_f64": round(fsai_bytes64 / (fsai_ms * 1e-3) / 1e9, 1) if fsai_ms else None,
             "fsai_apply_bf16": round(fsai_bytes16 / (fsai16_ms * 1e-3) / 1e9, 1) if fsai16_ms else None},
-        "roofline": {"kernel": "spmv_pq_kernel<double,double> (SELL-32 SpMV + p.q, FP64)",
-                     "bound": "hbm", "achieved": round(gbs, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+        "roofline": {"kernel": roof_kernel,
+                     "bound": "hbm", "achieved": round(roof_gbs, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(roof_gbs / peak, 4),
                      "peak_kind": f"{peak_kind} burst copy",
                      "traffic": traffic,
-                     "algorithmic_bytes": bytes64},
+                     "algorithmic_bytes": int(roof_bytes),
+                     "duration_ms": round(roof_ms, 5)},
         "e2e": {"value": round(statistics.mean(e_times), 4), "unit": "ms",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(round(launches)),
