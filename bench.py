@@ -84,6 +84,9 @@ class ClockSampler:
         self.proc = None
 
     def __enter__(self):
+        import threading
+        self.lines = []
+        first = threading.Event()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device),
@@ -92,17 +95,29 @@ class ClockSampler:
                 stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                self.lines.append(line)
+                first.set()
+            first.set()
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        # nvidia-smi's start-up (driver queries) must not overlap the timed
+        # region: wait for its first sample
+        first.wait(timeout=10.0)
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                self.out = ""
+            self.thread.join(timeout=5)
+        self.out = "".join(getattr(self, "lines", []))
 
     def summary(self):
         sm, smax, reasons = [], [], set()

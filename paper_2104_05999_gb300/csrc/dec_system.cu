@@ -186,7 +186,13 @@ fsai_setup_list_kernel(const int32_t* __restrict__ rows, const int32_t* __restri
 // (element e of thread t at A[e * blockDim + t]) so that accesses do not
 // conflict.  Rows with k > kFsaiThread go to a list for the warp-per-row
 // kernel above.
-constexpr int kFsaiThread = 16;
+// k <= 12 covers ~97% of the rows of the Delaunay meshes here (p99 13, max
+// 14); 78 packed doubles per thread let 5 blocks of 64 threads share an SM
+// (16 allowed only 3: the kernel waits on shared memory and FP64 latency)
+#ifndef DEC_FSAI_THREAD_K
+#define DEC_FSAI_THREAD_K 12
+#endif
+constexpr int kFsaiThread = DEC_FSAI_THREAD_K;
 constexpr int kFsaiTpb = 64;
 constexpr int kPacked = kFsaiThread * (kFsaiThread + 1) / 2;
 
@@ -332,11 +338,12 @@ dec_status build_precond(dec_ctx* ctx, int vs) {
   DEC_TRY(cudaFuncSetAttribute(fsai_setup_thread_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned gt = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((n + kFsaiTpb - 1) / kFsaiTpb, (int64_t)ctx->num_sms * 3));
+      1, std::min<int64_t>((n + kFsaiTpb - 1) / kFsaiTpb,
+                           (int64_t)ctx->num_sms * std::max<int64_t>(1, (220 << 10) / smem)));
   fsai_setup_thread_kernel<<<gt, kFsaiTpb, smem, s>>>(
       n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->pos_up.p, val, g,
       ctx->big_rows.p, big_count);
-  fsai_setup_list_kernel<<<(unsigned)ctx->num_sms, 32 * kFsaiWarps, 0, s>>>(
+  fsai_setup_list_kernel<<<(unsigned)ctx->num_sms * 4, 32 * kFsaiWarps, 0, s>>>(
       ctx->big_rows.p, big_count, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p,
       ctx->pos_up.p, val, g, ctx->errflag.p);
   DEC_TRY(cudaGetLastError());
