@@ -17,6 +17,9 @@ Section map
   Sec. 2.3 / Sec. 3.1 (Krylov solve to rel. tolerance 1e-10) -> pcg
   Sec. 2.5 (effective conductivity = flux through a Dirichlet face) -> k_eff
   Sec. 3.1 (Eq. 14, volume-weighted RMS error over tets) -> rms_error
+  Sec. 2.5, 3.3, 3.4 (crack growth: the max-flux face or a random face
+           cracks at each step, k_eff after each) -> crackable_edges,
+           crack_evolution
 
 Readings of the paper this oracle takes (each also listed with the library):
   * unknowns live on nodes: L = d0^T *1 d0 (the primal Darcy form the paper
@@ -44,6 +47,7 @@ __all__ = [
     "circumcentre_tri", "hodge_pieces", "hodge_star1", "dual_volumes",
     "crack_rho", "edge_crack_state", "laplacian", "full_laplacian",
     "jacobi", "fsai_factor", "pcg", "k_eff", "rms_error", "solve_path",
+    "crackable_edges", "crack_evolution",
 ]
 
 DIRICHLET = 1
@@ -486,6 +490,84 @@ def k_eff(xyz, E, w, T, tags):
     x0 = dirich & (xyz[:, 0] == 0.0)
     x1 = dirich & (xyz[:, 0] == 1.0)
     return out[x0].sum(), -out[x1].sum(), np.sum(w * (T[i] - T[j]) ** 2)
+
+
+# ---------------------------------------------------------------------------
+# Crack evolution (Sec. 2.5, Sec. 3.3, Sec. 3.4)
+# ---------------------------------------------------------------------------
+
+def crackable_edges(w):
+    """Edges whose dual face may crack.  The paper cracks the faces that lie
+    between two cells (its non-boundary faces); in the node form every dual
+    face separates the dual cells of the edge's two end points, so every
+    edge that still carries conductance (w > 0) is a candidate."""
+    return np.asarray(w) > 0.0
+
+
+def crack_evolution(xyz, tets, tags, T0, k=None, rule="max_flux",
+                    max_steps=100, order=None, precond="fsai", rtol=1e-13,
+                    k_stop=1e-9):
+    """A sequence of steady solutions with one more crack each (Sec. 2.5):
+
+    * rule "max_flux" (Sec. 3.3, deterministic): crack the uncracked
+      crackable edge whose dual face carries the largest flux |w_e (T_i -
+      T_j)| in the current solution (the value of the flux 2-form on that
+      face); the smallest edge id wins a tie;
+    * rule "order" (Sec. 3.4, stochastic): crack order[s] at step s (the
+      caller draws the random sequence).
+
+    Cracking sets the edge's conductance to 0.  Each step re-solves from
+    scratch and records k_eff; the loop ends after max_steps, when no
+    candidate is left, or once k_eff <= k_stop * k_eff(uncracked) (the domain
+    no longer conducts).  Returns dict(cracked, k_eff, k_eff0, T, w, E).
+    """
+    n = len(xyz)
+    tags = np.asarray(tags)
+    T0 = np.asarray(T0, dtype=np.float64).reshape(-1)
+    E, t2e = edge_list(tets)
+    w = hodge_star1(xyz, tets, E, t2e, k)
+    cand = crackable_edges(w)
+    dirich = tags == DIRICHLET
+
+    def solve(wc):
+        L, b, _ = laplacian(n, E, wc, tags, T0)
+        if precond == "jacobi":
+            dinv = jacobi(L)
+            M = lambda r: dinv * r                 # noqa: E731
+        else:
+            G = fsai_factor(L)
+            Gt = G.T.tocsr()
+            M = lambda r: Gt @ (G @ r)             # noqa: E731
+        u, _, _ = pcg(L, b[0], M, rtol)
+        T = u + np.where(dirich, T0, 0.0)
+        return T, k_eff(xyz, E, wc, T, tags)[0]
+
+    wc = w.copy()
+    T, k0 = solve(wc)
+    cracked, keff = [], []
+    for step in range(max_steps):
+        if rule == "max_flux":
+            live = np.flatnonzero(cand & (wc != 0.0))
+            if len(live) == 0:
+                break
+            flux = np.abs(wc[live] * (T[E[live, 0]] - T[E[live, 1]]))
+            e = int(live[np.argmax(flux)])        # first maximum: smallest id
+        elif rule == "order":
+            if order is None or step >= len(order):
+                break
+            e = int(order[step])
+            if not (0 <= e < len(E)) or not cand[e] or wc[e] == 0.0:
+                raise ValueError(f"order[{step}] = {e} is not an uncracked crackable edge")
+        else:
+            raise ValueError(f"unknown rule {rule}")
+        wc[e] = 0.0
+        cracked.append(e)
+        T, q = solve(wc)
+        keff.append(q)
+        if q <= k_stop * k0:
+            break
+    return dict(cracked=np.array(cracked, dtype=np.int64), k_eff=np.array(keff),
+                k_eff0=k0, T=T, w=wc, E=E)
 
 
 def rms_error(xyz, tets, T, T_exact):

@@ -406,3 +406,103 @@ def test_isolated_node_becomes_identity_row():
     assert iso[free] and iso.sum() == 1
     assert L[free, free] == 1.0 and b[0, free] == 0.0
     assert node_tags(wl.xyz)[free] == 0
+
+
+# ----------------------------------------------------- crack evolution
+
+def _dense_T(wl, E, w):
+    """Dirichlet solve by dense elimination (independent of PCG)."""
+    Lf = O.full_laplacian(wl.n, E, w).toarray()
+    D = wl.tags == 1
+    F = ~D
+    T = wl.T0[0].copy()
+    A = Lf[np.ix_(F, F)]
+    rhs = -Lf[np.ix_(F, D)] @ T[D]
+    # rows of nodes cut off from everything are zero: keep their T at 0
+    iso = np.abs(A).sum(axis=1) == 0.0
+    A[iso, iso] = 1.0
+    T[F] = np.linalg.solve(A, rhs)
+    return T
+
+
+def _x_faces_connected(wl, E, w):
+    from scipy.sparse.csgraph import connected_components
+    keep = w > 0.0
+    G = sp.coo_matrix((np.ones(keep.sum()), (E[keep, 0], E[keep, 1])),
+                      shape=(wl.n, wl.n))
+    _, lab = connected_components(G, directed=False)
+    x = wl.xyz[:, 0]
+    return bool(np.intersect1d(lab[x == 0.0], lab[x == 1.0]).size)
+
+
+def test_max_flux_crack_is_the_largest_face_flux():
+    # Sec. 3.3: the face carrying the largest flux cracks first; flux of the
+    # dual face of e = |w_e (T_i - T_j)|, here from a dense solve and a loop
+    wl = make_workload("lognormal64", N=5)
+    E, t2e = O.edge_list(wl.tets)
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e, wl.k)
+    T = _dense_T(wl, E, w)
+    best, best_e = -1.0, -1
+    for e in range(len(E)):
+        if w[e] > 0.0:
+            f = abs(w[e] * (T[E[e, 0]] - T[E[e, 1]]))
+            if f > best:
+                best, best_e = f, e
+    out = O.crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], k=wl.k,
+                            max_steps=1)
+    assert out["cracked"].tolist() == [best_e]
+    w1 = w.copy()
+    w1[best_e] = 0.0
+    T1 = _dense_T(wl, E, w1)
+    q = O.k_eff(wl.xyz, E, w1, T1, wl.tags)[0]
+    assert out["k_eff"][0] == pytest.approx(q, rel=1e-10)
+
+
+def test_crack_growth_is_monotone_and_ends_at_separation():
+    # removing conductance never raises k_eff (Rayleigh monotonicity); the
+    # loop ends exactly when the cracks separate x = 0 from x = 1
+    wl = make_workload("lognormal64", N=5)
+    out = O.crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], k=wl.k,
+                            max_steps=2000)
+    k = out["k_eff"]
+    assert (np.diff(k) <= 1e-12 * out["k_eff0"]).all()
+    assert k[-1] <= 1e-9 * out["k_eff0"] < k[-2]
+    E, w = out["E"], out["w"]
+    assert not _x_faces_connected(wl, E, w)
+    w_prev = w.copy()
+    w_prev[out["cracked"][-1]] = O.hodge_star1(
+        wl.xyz, wl.tets, E, O.edge_list(wl.tets)[1], wl.k)[out["cracked"][-1]]
+    assert _x_faces_connected(wl, E, w_prev)
+
+
+def test_kuhn_separation_needs_the_min_cut():
+    # on the Kuhn lattice the conducting edges form the cubic grid (the
+    # diagonals carry *1 = 0), whose smallest x = 0 / x = 1 cut has N^2 edges
+    # (N^2 disjoint straight paths, Menger): no rule separates it sooner
+    N = 4
+    wl = make_workload("kuhn9", N=N)
+    out = O.crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], k=None,
+                            precond="jacobi", max_steps=500)
+    assert len(out["cracked"]) >= N * N
+    assert not _x_faces_connected(wl, out["E"], out["w"])
+
+
+def test_ordered_cracks_equal_cutting_them_at_once():
+    # Sec. 3.4: the stochastic rule cracks a given random sequence; the end
+    # state equals a solve with all those conductances set to 0
+    wl = make_workload("lognormal64", N=5)
+    E, t2e = O.edge_list(wl.tets)
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e, wl.k)
+    rng = np.random.default_rng(7)
+    order = rng.permutation(np.flatnonzero(O.crackable_edges(w)))[:12]
+    out = O.crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], k=wl.k,
+                            rule="order", order=order, max_steps=12)
+    assert out["cracked"].tolist() == order.tolist()
+    w12 = w.copy()
+    w12[order] = 0.0
+    T = _dense_T(wl, E, w12)
+    assert out["k_eff"][-1] == pytest.approx(O.k_eff(wl.xyz, E, w12, T, wl.tags)[0],
+                                             rel=1e-10)
+    with pytest.raises(ValueError):
+        O.crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], k=wl.k,
+                          rule="order", order=[order[0], order[0]], max_steps=2)
