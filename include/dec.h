@@ -192,6 +192,42 @@ dec_status dec_solve(dec_ctx* ctx, double rtol, int32_t max_iter, int32_t mode,
  * For T0 = 1 on x = 0 and 0 on x = 1 in the unit cube, k_eff = q_in. */
 dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy);
 
+/* crack rules (dec_crack_evolve) */
+enum {
+  DEC_CRACK_MAX_FLUX = 0,   /* the face with the largest flux cracks (Sec. 3.3)   */
+  DEC_CRACK_ORDER = 1       /* faces crack in a caller-drawn order (Sec. 3.4)     */
+};
+
+/* Crack growth (Sec. 2.5; deterministic cracking Sec. 3.3, stochastic
+ * cracking Sec. 3.4).  Starting from the current state (after
+ * dec_laplacian_build with one Dirichlet set, no crack states and
+ * DEC_PRECOND_JACOBI or DEC_PRECOND_FSAI), solve, then repeat: crack one
+ * dual face (its edge's *1 becomes 0 for L, b, the preconditioner and
+ * k_eff), rebuild L and the preconditioner, solve again from zero, record
+ * k_eff.  Candidates are the edges that still conduct (*1 > 0, not cut):
+ * in the node form every dual face lies between two dual cells.
+ *   rule      DEC_CRACK_MAX_FLUX: the candidate with the largest
+ *             |*1_e (T_i - T_j)| in the current solution (the flux 2-form on
+ *             its dual face; the smallest edge id wins a tie);
+ *             DEC_CRACK_ORDER: edge order[s] at step s.
+ *   max_steps at most this many cracks.
+ *   order     [max_steps] int32 edge ids (dec_get_edges numbering), host or
+ *             device; only read for DEC_CRACK_ORDER, else may be NULL.
+ *   rtol, max_iter, mode   as for dec_solve (FP64, MIXED or MIXED_PHASED).
+ *   k_stop    stop after the step whose k_eff <= k_stop * k_eff(uncracked)
+ *             (e.g. 1e-9: the domain no longer conducts).
+ *   cracked   [max_steps] int32 host: edge cracked at each step.
+ *   k_eff     [max_steps] f64 host: q_in (as dec_k_eff) after each step.
+ *   steps     host: number of steps done (fewer than max_steps when k_stop
+ *             is reached or no candidate is left).
+ * The cracks stay in the context (dec_get_hodge shows them as cut in state
+ * 0; dec_k_eff reports the last state).  Errors: DEC_ERR_STATE, DEC_ERR_ARG
+ * (also for an order entry that is not a conducting, uncut edge; the steps
+ * before it are kept), and the errors of dec_solve. */
+dec_status dec_crack_evolve(dec_ctx* ctx, int32_t rule, int32_t max_steps,
+                            const int32_t* order, double rtol, int32_t max_iter, int32_t mode,
+                            double k_stop, int32_t* cracked, double* k_eff, int32_t* steps);
+
 /* ---- sizes and intermediate results (parity checks, debugging) ---- */
 
 /* n_nodes, n_tets, n_edges, nnz of L (with the diagonal), instances B. */

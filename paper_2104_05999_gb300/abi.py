@@ -35,6 +35,7 @@ DEC_PRECOND_JACOBI, DEC_PRECOND_FSAI, DEC_PRECOND_FSAI_SHARED = 0, 1, 2
 DEC_MODE_FP64, DEC_MODE_MIXED, DEC_MODE_MIXED_PHASED, DEC_MODE_MIXED_BATCHED = 0, 1, 2, 3
 DEC_KERNEL_SPMV_F64, DEC_KERNEL_SPMV_F32 = 0, 1
 DEC_KERNEL_FSAI_F64, DEC_KERNEL_FSAI_BF16 = 2, 3
+DEC_CRACK_MAX_FLUX, DEC_CRACK_ORDER = 0, 1
 
 _P = C.c_void_p
 _I64 = C.c_int64
@@ -50,6 +51,7 @@ SIGNATURES = {
     "dec_laplacian_build": [_P, _P, _I32, _I32],
     "dec_solve": [_P, _D, _I32, _I32, _P, _P, _P],
     "dec_k_eff": [_P, _P, _P, _P],
+    "dec_crack_evolve": [_P, _I32, _I32, _P, _D, _I32, _I32, _D, _P, _P, _P],
     "dec_get_sizes": [_P, _P, _P, _P, _P, _P],
     "dec_get_edges": [_P, _P, _P],
     "dec_get_hodge": [_P, _P, _P],
@@ -182,6 +184,28 @@ class Context:
         self._check(self.lib.dec_k_eff(self.h, q_in.ctypes.data,
                                        q_out.ctypes.data, energy.ctypes.data))
         return q_in, q_out, energy
+
+    def dec_crack_evolve(self, rule, max_steps, order=None, rtol=1e-10,
+                         max_iter=100000, mode=DEC_MODE_FP64, k_stop=1e-9,
+                         raise_on_error=True):
+        """Crack growth from the current state; returns (status, cracked
+        edge per step, k_eff per step), trimmed to the steps done."""
+        cracked = np.zeros(max(max_steps, 1), dtype=np.int32)
+        keff = np.zeros(max(max_steps, 1))
+        steps = C.c_int32(0)
+        keep = None
+        optr = None
+        if order is not None:
+            keep = np.ascontiguousarray(order, dtype=np.int32)
+            optr = keep.ctypes.data
+        st = self.lib.dec_crack_evolve(self.h, int(rule), int(max_steps), optr,
+                                       float(rtol), int(max_iter), int(mode),
+                                       float(k_stop), cracked.ctypes.data,
+                                       keff.ctypes.data, C.byref(steps))
+        if raise_on_error:
+            self._check(st)
+        k = steps.value
+        return st, cracked[:k].copy(), keff[:k].copy()
 
     # ---- getters --------------------------------------------------------
     def sizes(self):

@@ -306,6 +306,46 @@ dec_status dec_solve(dec_ctx* ctx, double rtol, int32_t max_iter, int32_t mode,
   return worst;
 }
 
+dec_status dec_crack_evolve(dec_ctx* ctx, int32_t rule, int32_t max_steps,
+                            const int32_t* order, double rtol, int32_t max_iter, int32_t mode,
+                            double k_stop, int32_t* cracked, double* k_eff, int32_t* steps) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 3) return ctx->fail(DEC_ERR_STATE, "crack_evolve: no Laplacian built");
+  if (ctx->B != 1 || ctx->n_scales != 1 || ctx->precond == DEC_PRECOND_FSAI_SHARED)
+    return ctx->fail(DEC_ERR_STATE,
+                     "crack_evolve: needs one instance (one Dirichlet set, no crack states) "
+                     "and a per-instance preconditioner");
+  if (rule != DEC_CRACK_MAX_FLUX && rule != DEC_CRACK_ORDER)
+    return ctx->fail(DEC_ERR_ARG, "crack_evolve: unknown rule");
+  if (mode != DEC_MODE_FP64 && mode != DEC_MODE_MIXED && mode != DEC_MODE_MIXED_PHASED)
+    return ctx->fail(DEC_ERR_ARG, "crack_evolve: mode must be FP64, MIXED or MIXED_PHASED");
+  if (max_steps < 0 || !cracked || !k_eff || !steps || (rule == DEC_CRACK_ORDER && !order && max_steps > 0))
+    return ctx->fail(DEC_ERR_ARG, "crack_evolve: bad max_steps or NULL output / order");
+  if (!(rtol > 0.0) || !std::isfinite(rtol) || max_iter < 1 || !(k_stop >= 0.0))
+    return ctx->fail(DEC_ERR_ARG, "crack_evolve: rtol > 0, max_iter >= 1, k_stop >= 0");
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  std::vector<int32_t> ord;
+  if (rule == DEC_CRACK_ORDER) DEC_TRY(host_copy(ord, order, max_steps, s));
+  DEC_TRY(ctx->u.ensure((size_t)n));
+  DEC_TRY(ctx->out3.ensure(4));
+  if (mode == DEC_MODE_FP64) {
+    for (auto* bf : {&ctx->x64, &ctx->r64, &ctx->z64, &ctx->p64, &ctx->q64, &ctx->t64})
+      DEC_TRY(bf->ensure(n));
+  } else {
+    for (auto* bf : {&ctx->x64, &ctx->r64, &ctx->t64}) DEC_TRY(bf->ensure(n));
+    for (auto* bf : {&ctx->x32, &ctx->r32, &ctx->z32, &ctx->p32, &ctx->q32, &ctx->t32})
+      DEC_TRY(bf->ensure(n));
+  }
+  ctx->stage = 3;
+  dec_status st = dec::crack_evolve(ctx, rule, max_steps, ord.data(), rtol, max_iter, mode,
+                                    k_stop, cracked, k_eff, steps);
+  if (st == DEC_OK) ctx->stage = 4;   // the last state's solution is current
+  return st;
+}
+
 dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy) {
   if (!ctx) return DEC_ERR_ARG;
   ctx->err.clear();

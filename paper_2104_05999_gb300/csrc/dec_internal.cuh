@@ -140,6 +140,7 @@ struct dec_ctx {
   dec::DevBuf<float> bw32;
   dec::DevBuf<double> bw64, bb, bx64, br64, bpartial;
   dec::DevBuf<uint8_t> bfc;
+  dec::DevBuf<int64_t> crack_buf;          // crack growth: block bests, picked edge
   dec::DevBuf<__nv_bfloat16> bg16, bgb;   // shared factor, per-instance factors
   bool batch_per_instance = false;
   dec::DevBuf<float> bx, br, bz, bp, bq, bt;
@@ -165,7 +166,7 @@ struct dec_ctx {
     sGlo64.release(); sGup64.release(); sL32.release(); sGlo16.release();
     sGup16.release(); big_rows.release(); coop.release(); bw32.release();
     bw64.release(); bb.release(); bx64.release(); br64.release(); bpartial.release();
-    bfc.release(); bg16.release(); bx.release(); br.release(); bz.release();
+    bfc.release(); crack_buf.release(); bg16.release(); bx.release(); br.release(); bz.release();
     bp.release(); bq.release(); bt.release(); bgb.release();
   }
 
@@ -331,4 +332,8 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
                        double* avg_ms);
 // shared-memory limits of the staged SELL kernels (current device)
 cudaError_t init_kernel_attributes();
+// crack growth
+dec_status crack_evolve(dec_ctx* ctx, int rule, int max_steps, const int32_t* order_host,
+                        double rtol, int max_iter, int mode, double k_stop, int32_t* cracked,
+                        double* k_eff, int32_t* steps);
 }  // namespace dec
