@@ -378,6 +378,35 @@ def gpu_arm(args, rank, world):
 KERNEL_REV = "r1"
 
 
+def crack_growth_measure(max_steps=600, oracle_steps=3):
+    """Crack growth (max-flux rule) on a mesh of the size of the paper's
+    crack study (a 15^3 jittered Delaunay cube, 3,375 nodes, k = 1): GPU
+    time per step (crack + rebuild + solve + k_eff) over up to max_steps
+    steps, and the oracle's time per step over a few steps on the host."""
+    import oracle as O
+    from dec_inputs import make_workload
+    from paper_2104_05999_gb300 import abi
+    wl = make_workload("lognormal64", N=15)
+    ctx = abi.Context(device=int(os.environ.get("LOCAL_RANK", 0)))
+    ctx.dec_mesh_upload(wl.xyz, wl.tets, wl.tags)
+    ctx.dec_hodge_assemble(None)
+    ctx.dec_laplacian_build(wl.T0[:1], abi.DEC_PRECOND_FSAI)
+    t0 = time.perf_counter()
+    _, cracked, keff = ctx.dec_crack_evolve(abi.DEC_CRACK_MAX_FLUX, max_steps, rtol=1e-10)
+    dt = time.perf_counter() - t0
+    ctx.close()
+    t0 = time.perf_counter()
+    O.crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], k=None,
+                      max_steps=oracle_steps, rtol=1e-10)
+    ot = (time.perf_counter() - t0) / (oracle_steps + 1)   # + the first solve
+    return {"mesh": f"15^3 jittered Delaunay cube, k = 1 ({wl.n} nodes, {wl.m} tets)",
+            "rule": "max_flux", "steps": int(len(cracked)),
+            "ms_per_step": round(1000 * dt / max(1, len(cracked)), 3),
+            "k_eff_after_first": float(keff[0]), "k_eff_last": float(keff[-1]),
+            "oracle_ms_per_step": round(1000 * ot, 1),
+            "oracle": "oracle.crack_evolution, numpy/scipy FP64, 1 thread"}
+
+
 # ------------------------------------------------------------- CPU oracle
 def oracle_sample(wl, m_sample, pcg_iters, target_iters):
     """Time the oracle's full path on the sub-mesh made of the first
@@ -488,6 +517,7 @@ def main():
             out["cpu_baseline"] = {"value": round(ms, 1), "unit": "ms",
                                    "cores": 1, "kind": "oracle",
                                    "sample": desc}
+            out["crack_growth"] = crack_growth_measure()
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
