@@ -158,10 +158,86 @@ __device__ __forceinline__ void set4(float4& v, int j, float x) {
   if (j == 0) v.x = x; else if (j == 1) v.y = x; else if (j == 2) v.z = x; else v.w = x;
 }
 
-// (L_b x)_i for the four instances 4q..4q+3 of row i (FP32).  Entries are
+// The gathers of the FP32 row products go to shared memory with 16-byte
+// asynchronous copies: registers (64 per thread at 1024 threads per SM) do
+// not bound the gathers in flight, so a row takes ceil(entries / kGU) round
+// trips instead of ceil(entries / 4).  Slot u of thread t is
+// slots[u * 1024 + t] (conflict-free 16-byte accesses); a thread reads only
+// its own slots, so no barrier is needed.
+#ifndef DEC_BATCH_GU
+#define DEC_BATCH_GU 6
+#endif
+#ifndef DEC_BATCH_ASYNC_MIN_BS
+#define DEC_BATCH_ASYNC_MIN_BS 32
+#endif
+constexpr int kAsyncMinBS = DEC_BATCH_ASYNC_MIN_BS;
+constexpr int kGU = DEC_BATCH_GU;
+constexpr int kGatherSmem = kGU * kBBlock * (int)sizeof(float4);
+
+__device__ __forceinline__ float4* gather_slots() {
+  extern __shared__ __align__(16) float4 bsm_slots[];
+  return bsm_slots + threadIdx.x;
+}
+__device__ __forceinline__ void gather_async(float4* slot, const float4* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(slot);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void gather_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// (L_b x)_i for the four instances 4q..4q+3 of row i (FP32).  The diagonal
+// slot carries w = 0, so it needs no test.
+__device__ __forceinline__ float4 edge_form4_async(const BatchArgs& a, int64_t i, int q,
+                                             const int (&st)[kIPT],
+                                             const float4* __restrict__ X) {
+  const int TPR = a.BS / kIPT;
+  float4* slots = gather_slots();
+  const float4 xi = X[i * TPR + q];
+  if (a.tag[i] == DEC_NODE_DIRICHLET) return xi;
+  const int32_t k0 = a.rowptr[i], k1 = a.rowptr[i + 1];
+  float acc[kIPT] = {0.f, 0.f, 0.f, 0.f}, dsum[kIPT] = {0.f, 0.f, 0.f, 0.f};
+  for (int32_t k = k0; k < k1; k += kGU) {
+    const int cnt = k1 - k < kGU ? k1 - k : kGU;
+    int32_t c[kGU];
+#pragma unroll
+    for (int u = 0; u < kGU; ++u) c[u] = u < cnt ? __ldg(a.col + k + u) : 0;
+#pragma unroll
+    for (int u = 0; u < kGU; ++u)
+      if (u < cnt) gather_async(slots + u * kBBlock, X + (int64_t)c[u] * TPR + q);
+    float wv[kGU];
+    int f[kGU];
+#pragma unroll
+    for (int u = 0; u < kGU; ++u) {
+      wv[u] = u < cnt ? __ldg(a.w32 + k + u) : 0.0f;
+      f[u] = u < cnt ? (int)__ldg(a.fc + k + u) : 0;
+    }
+    gather_wait();
+#pragma unroll
+    for (int u = 0; u < kGU; ++u) {
+      if (u < cnt) {
+        const float4 xv = slots[u * kBBlock];
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) {
+          const float m = f[u] > st[j] ? wv[u] : 0.0f;
+          dsum[j] += m;
+          acc[j] = fmaf(m, get4(xv, j), acc[j]);
+        }
+      }
+    }
+  }
+  float4 y;
+#pragma unroll
+  for (int j = 0; j < kIPT; ++j)
+    set4(y, j, dsum[j] == 0.0f ? get4(xi, j) : fmaf(dsum[j], get4(xi, j), -acc[j]));
+  return y;
+}
+
+// (L_b x)_i for the four instances 4q..4q+3 of row i (FP32), gathers into
+// registers 4 at a time (the path for small instance strides).  Entries are
 // taken 4 at a time: structure loads, then 4 independent 16-byte gathers.
 // The diagonal slot carries w = 0, so it needs no test.
-__device__ __forceinline__ float4 edge_form4(const BatchArgs& a, int64_t i, int q,
+__device__ __forceinline__ float4 edge_form4_reg(const BatchArgs& a, int64_t i, int q,
                                              const int (&st)[kIPT],
                                              const float4* __restrict__ X) {
   constexpr int U = 4;
@@ -232,8 +308,53 @@ __device__ __forceinline__ void edge_form4_64(const BatchArgs& a, int64_t i, int
 }
 
 // FSAI halves (lower: G, upper: G^T) for four instances; per-instance
-// factors (gb) or the shared one (g)
-__device__ __forceinline__ float4 fsai4(const BatchArgs& a, int64_t i, int q, bool lower,
+// factors (gb) or the shared one (g); gathers as in edge_form4
+__device__ __forceinline__ float4 fsai4_async(const BatchArgs& a, int64_t i, int q, bool lower,
+                                        const float4* __restrict__ X) {
+  const int BS = a.BS, TPR = BS / kIPT;
+  float4* slots = gather_slots();
+  const int32_t k0 = lower ? a.rowptr[i] : a.dpos[i];
+  const int32_t k1 = lower ? a.dpos[i] + 1 : a.rowptr[i + 1];
+  float acc[kIPT] = {0.f, 0.f, 0.f, 0.f};
+  for (int32_t k = k0; k < k1; k += kGU) {
+    const int cnt = k1 - k < kGU ? k1 - k : kGU;
+    int32_t c[kGU];
+#pragma unroll
+    for (int u = 0; u < kGU; ++u) c[u] = u < cnt ? __ldg(a.col + k + u) : 0;
+#pragma unroll
+    for (int u = 0; u < kGU; ++u)
+      if (u < cnt) gather_async(slots + u * kBBlock, X + (int64_t)c[u] * TPR + q);
+    uint2 graw[kGU];
+#pragma unroll
+    for (int u = 0; u < kGU; ++u) {
+      if (u >= cnt) {
+        graw[u] = make_uint2(0u, 0u);
+      } else if (a.gb) {
+        graw[u] = *reinterpret_cast<const uint2*>(a.gb + (int64_t)(k + u) * BS + kIPT * q);
+      } else {
+        const unsigned bits = __bfloat16_as_ushort(a.g[k + u]);
+        graw[u] = make_uint2(bits | (bits << 16), bits | (bits << 16));
+      }
+    }
+    gather_wait();
+#pragma unroll
+    for (int u = 0; u < kGU; ++u) {
+      if (u < cnt) {
+        const float4 xv = slots[u * kBBlock];
+        const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&graw[u].x);
+        const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&graw[u].y);
+        acc[0] = fmaf(__low2float(lo), xv.x, acc[0]);
+        acc[1] = fmaf(__high2float(lo), xv.y, acc[1]);
+        acc[2] = fmaf(__low2float(hi), xv.z, acc[2]);
+        acc[3] = fmaf(__high2float(hi), xv.w, acc[3]);
+      }
+    }
+  }
+  return make_float4(acc[0], acc[1], acc[2], acc[3]);
+}
+
+// FSAI halves with register gathers (small instance strides)
+__device__ __forceinline__ float4 fsai4_reg(const BatchArgs& a, int64_t i, int q, bool lower,
                                         const float4* __restrict__ X) {
   constexpr int U = 4;
   const int BS = a.BS, TPR = BS / kIPT;
@@ -274,6 +395,20 @@ __device__ __forceinline__ float4 fsai4(const BatchArgs& a, int64_t i, int q, bo
   return make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
+// Row products of the kernel: shared-memory gathers (ASYNC) or registers
+template <bool ASYNC>
+__device__ __forceinline__ float4 edge_form4(const BatchArgs& a, int64_t i, int q,
+                                             const int (&st)[kIPT], const float4* X) {
+  if constexpr (ASYNC) return edge_form4_async(a, i, q, st, X);
+  else return edge_form4_reg(a, i, q, st, X);
+}
+template <bool ASYNC>
+__device__ __forceinline__ float4 fsai4(const BatchArgs& a, int64_t i, int q, bool lower,
+                                        const float4* X) {
+  if constexpr (ASYNC) return fsai4_async(a, i, q, lower, X);
+  else return fsai4_reg(a, i, q, lower, X);
+}
+
 // Dot-product accumulator: FP32 products folded into FP64 every 16 terms,
 // so the narrow FP64 pipe sees one add per 16 elements.
 struct Acc2 {
@@ -287,6 +422,7 @@ struct Acc2 {
   __device__ __forceinline__ double get() const { return d + (double)f; }
 };
 
+template <bool ASYNC>
 __global__ void __launch_bounds__(kBBlock, 1)
 pcg_batched_persistent(BatchArgs a) {
   __shared__ BState S;
@@ -352,13 +488,13 @@ pcg_batched_persistent(BatchArgs a) {
   for (;;) {
     // ---- segment start for the active instances: z = M r, p = z + beta p
     if (any4(S.active))
-      for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4(a, i, q, true, R);
+      for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4<ASYNC>(a, i, q, true, R);
     if (!bgrid_sync(a.bar, err)) return;
     {
       Acc2 acc[kIPT];
       if (any4(S.active))
         for (int64_t i = row0; i < n; i += rstep) {
-          const float4 zi = fsai4(a, i, q, false, T);
+          const float4 zi = fsai4<ASYNC>(a, i, q, false, T);
           Z[i * TPR + q] = zi;
           const float4 ri = R[i * TPR + q];
 #pragma unroll
@@ -395,7 +531,7 @@ pcg_batched_persistent(BatchArgs a) {
         Acc2 acc[kIPT];
         if (any4(S.iterating))
           for (int64_t i = row0; i < n; i += rstep) {
-            const float4 qi = edge_form4(a, i, q, st, Pv);
+            const float4 qi = edge_form4<ASYNC>(a, i, q, st, Pv);
             Q[i * TPR + q] = qi;
             const float4 pi = Pv[i * TPR + q];
 #pragma unroll
@@ -455,13 +591,13 @@ pcg_batched_persistent(BatchArgs a) {
       if (S.count == 0) break;
       // preconditioner on the iterating instances
       if (any4(S.iterating))
-        for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4(a, i, q, true, R);
+        for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4<ASYNC>(a, i, q, true, R);
       if (!bgrid_sync(a.bar, err)) return;
       {
         Acc2 acc[kIPT];
         if (any4(S.iterating))
           for (int64_t i = row0; i < n; i += rstep) {
-            const float4 zi = fsai4(a, i, q, false, T);
+            const float4 zi = fsai4<ASYNC>(a, i, q, false, T);
             Z[i * TPR + q] = zi;
             const float4 ri = R[i * TPR + q];
 #pragma unroll
@@ -806,8 +942,14 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   if (B > kBMax) return ctx->fail(DEC_ERR_LIMIT, "batched solve: more than 64 instances");
   int coop = 0, per_sm = 0;
   DEC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
-  DEC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_batched_persistent,
-                                                        kBBlock, 0));
+  // shared-memory gathers pay from 8 threads per row (BS >= 32); with fewer
+  // threads per row the L1 they give up costs more than they gain
+  const bool async = BS >= kAsyncMinBS;
+  const void* kern = async ? (const void*)pcg_batched_persistent<true>
+                           : (const void*)pcg_batched_persistent<false>;
+  const int smem = async ? kGatherSmem : 0;
+  DEC_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  DEC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBBlock, smem));
   if (!coop || per_sm < 1)
     return ctx->fail(DEC_ERR_LIMIT, "batched solve: cooperative launch unavailable");
   const int grid = ctx->num_sms;
@@ -850,8 +992,7 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   a.seg2 = 1e-4;
   a.max_iter = max_iter;
   void* args[] = {&a};
-  DEC_TRY(cudaLaunchCooperativeKernel((const void*)pcg_batched_persistent, dim3(grid),
-                                      dim3(kBBlock), args, 0, s));
+  DEC_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kBBlock), args, smem, s));
   ctx->launches += 1;
   const unsigned g2 = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((n * B + 255) / 256, (int64_t)ctx->num_sms * 16));
