@@ -74,7 +74,7 @@ enum {
                                    (DEC_MODE_MIXED_BATCHED): Dirichlet sets
                                    share the FSAI factor of their common L;
                                    crack states get one FP32-built BF16
-                                   factor each (rows longer than 16 keep the
+                                   factor each (rows longer than 12 keep the
                                    uncracked operator's factor)               */
 };
 /* solve modes (dec_solve) */

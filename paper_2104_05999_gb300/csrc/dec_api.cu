@@ -352,13 +352,12 @@ dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy) 
   if (ctx->stage < 4) return ctx->fail(DEC_ERR_STATE, "k_eff: no solution");
   if (!q_in) return ctx->fail(DEC_ERR_ARG, "k_eff: q_in is NULL");
   DEC_TRY_STATUS(set_device(ctx));
-  DEC_TRY(ctx->t64.ensure(ctx->n));
+  std::vector<double> o(3 * (size_t)ctx->B);
+  DEC_TRY_STATUS(dec::k_eff_all(ctx, o.data()));
   for (int inst = 0; inst < ctx->B; ++inst) {
-    double o[3];
-    DEC_TRY_STATUS(dec::k_eff_instance(ctx, inst, o));
-    q_in[inst] = o[0];
-    if (q_out) q_out[inst] = o[1];
-    if (energy) energy[inst] = o[2];
+    q_in[inst] = o[3 * inst];
+    if (q_out) q_out[inst] = o[3 * inst + 1];
+    if (energy) energy[inst] = o[3 * inst + 2];
   }
   return DEC_OK;
 }

@@ -700,9 +700,13 @@ pcg_batched_persistent(BatchArgs a) {
 // g / sqrt(g_i)), computed in FP32 from the edge form of L_b and stored in
 // BF16 with the instances contiguous per entry.  A group of BS threads
 // handles one row, thread b instance b, each with the packed lower triangle
-// of its block in shared memory (k <= kBFsaiMax).  Longer rows keep the
+// of its block in shared memory (k <= kBFsaiMax).  Longer rows (about 3 %
+// of the rows at a limit of 12, which lets two blocks share an SM) keep the
 // shared factor of the uncracked operator.
-constexpr int kBFsaiMax = 16;
+#ifndef DEC_BFSAI_MAX
+#define DEC_BFSAI_MAX 12
+#endif
+constexpr int kBFsaiMax = DEC_BFSAI_MAX;
 constexpr int kBFsaiTpb = 256;
 constexpr int kBPacked = kBFsaiMax * (kBFsaiMax + 1) / 2;
 

@@ -119,7 +119,8 @@ dec_status crack_evolve(dec_ctx* ctx, int rule, int max_steps, const int32_t* or
   auto solve = [&]() -> dec_status {
     dec_status st = solve_instance(ctx, 0, rtol, max_iter, mode, &it, &rr);
     if (st != DEC_OK) return st;
-    return k_eff_instance(ctx, 0, o);   // leaves T in t64
+    DEC_TRY_STATUS(form_T(ctx, 0, ctx->t64.p));   // T for the next pick
+    return k_eff_all(ctx, o);                     // as dec_k_eff reports it
   };
   DEC_TRY_STATUS(solve());
   const double k0 = o[0];

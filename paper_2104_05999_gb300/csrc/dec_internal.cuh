@@ -128,6 +128,7 @@ struct dec_ctx {
   dec::DevBuf<unsigned> ticket;
   dec::DevBuf<dec::CgScalars> cg;
   dec::DevBuf<double> out3;        // k_eff outputs [B][3]
+  dec::DevBuf<double> kpartial;    // k_eff block partials [3B][blocks]
   dec::DevBuf<uint8_t> flush;      // L2 eviction buffer (kernel timing only)
   // solver layouts (SELL-32-512) and their value arrays, per value set
   dec::SellLayout sellL, sellLo, sellUp;
@@ -166,7 +167,7 @@ struct dec_ctx {
     sGlo64.release(); sGup64.release(); sL32.release(); sGlo16.release();
     sGup16.release(); big_rows.release(); coop.release(); bw32.release();
     bw64.release(); bb.release(); bx64.release(); br64.release(); bpartial.release();
-    bfc.release(); crack_buf.release(); bg16.release(); bx.release(); br.release(); bz.release();
+    bfc.release(); kpartial.release(); crack_buf.release(); bg16.release(); bx.release(); br.release(); bz.release();
     bp.release(); bq.release(); bt.release(); bgb.release();
   }
 
@@ -321,7 +322,7 @@ dec_status build_values_uncracked(dec_ctx* ctx);
 // solve
 dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
                           int mode, int* iters, double* relres);
-dec_status k_eff_instance(dec_ctx* ctx, int inst, double* out3);
+dec_status k_eff_all(dec_ctx* ctx, double* out3_host);   // [B][3], one pass
 dec_status form_T(dec_ctx* ctx, int inst, double* T);
 dec_status solve_mixed_persistent(dec_ctx* ctx, int inst, double rtol, int max_iter,
                                   int* iters_out, double* relres_out);

@@ -385,6 +385,84 @@ cudaError_t init_kernel_attributes() {
   return e;
 }
 
+// k_eff pieces of every instance in one pass: block row blockIdx.y is
+// instance b (its crack state when `states`, its Dirichlet set when `sets`),
+// T = u_b + T0 on Dirichlet nodes formed on the fly; block partials go to
+// partial[(3 b + v) * gridDim.x + block] and k_eff_batch_sum_kernel adds them
+// in block order (deterministic).
+__global__ void __launch_bounds__(kBlock)
+k_eff_batch_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                   const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
+                   const int32_t* __restrict__ dpos, const uint8_t* __restrict__ tag,
+                   const double* __restrict__ xyz, const double* __restrict__ w,
+                   const uint8_t* __restrict__ fc, int states, int sets,
+                   const double* __restrict__ u, const double* __restrict__ T0,
+                   double* __restrict__ partial) {
+  __shared__ double sh[kBlock];
+  const int b = blockIdx.y;
+  const int state = states ? b : 0;
+  const double* ub = u + (int64_t)b * n;
+  const double* t0 = T0 + (sets ? (int64_t)b * n : 0);
+  auto Tof = [&](int64_t i) { return ub[i] + (tag[i] == DEC_NODE_DIRICHLET ? t0[i] : 0.0); };
+  double qin = 0.0, qout = 0.0, en = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double Ti = Tof(i);
+    const int32_t k0 = rowptr[i], k1 = rowptr[i + 1], kd = dpos[i];
+    double net = 0.0;
+    for (int32_t k = k0; k < k1; ++k) {
+      if (k == kd) continue;
+      const int32_t e = eid[k];
+      const double we = (int)fc[e] > state ? w[e] : 0.0;
+      const double d = Ti - Tof(col[k]);
+      net += we * d;
+      if (k > kd) en += we * d * d;
+    }
+    if (tag[i] == DEC_NODE_DIRICHLET) {
+      const double xi = xyz[3 * i];
+      if (xi == 0.0) qin += net;
+      else if (xi == 1.0) qout -= net;
+    }
+  }
+  const double v[3] = {qin, qout, en};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double t = block_sum<kBlock>(v[k], sh);
+    if (threadIdx.x == 0) partial[(3 * (int64_t)b + k) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_eff_batch_sum_kernel(int nblocks, int nvals, const double* __restrict__ partial,
+                                       double* __restrict__ out) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvals; v += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nblocks; ++k) s += partial[(int64_t)v * nblocks + k];
+    out[v] = s;
+  }
+}
+
+dec_status k_eff_all(dec_ctx* ctx, double* out3_host) {
+  const int64_t n = ctx->n;
+  const int B = ctx->B;
+  cudaStream_t s = ctx->stream;
+  const unsigned G = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)ctx->num_sms * 8 / std::max(1, B / 8 + 1)));
+  DEC_TRY(ctx->kpartial.ensure((size_t)3 * B * G));
+  DEC_TRY(ctx->out3.ensure(3 * (size_t)B + 1));
+  k_eff_batch_kernel<<<dim3(G, (unsigned)B), kBlock, 0, s>>>(
+      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->xyz.p, ctx->w.p,
+      ctx->first_cut.p, ctx->n_scales > 1, ctx->n_sets > 1, ctx->u.p, ctx->T0.p,
+      ctx->kpartial.p);
+  k_eff_batch_sum_kernel<<<(unsigned)((3 * B + 127) / 128), 128, 0, s>>>(
+      (int)G, 3 * B, ctx->kpartial.p, ctx->out3.p);
+  DEC_TRY(cudaGetLastError());
+  ctx->launches += 2;
+  DEC_TRY(cudaMemcpyAsync(out3_host, ctx->out3.p, 3 * sizeof(double) * B,
+                          cudaMemcpyDeviceToHost, s));
+  DEC_TRY(cudaStreamSynchronize(s));
+  return DEC_OK;
+}
+
 // ------------------------------------------------------------- driver
 constexpr int kChunk = 16;       // iterations per graph launch / host poll
 
@@ -601,27 +679,6 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
   *iters_out = total_iters;
   *relres_out = bnorm2 > 0.0 ? std::sqrt(rr_true / bnorm2) : 0.0;
   return st;
-}
-
-dec_status k_eff_instance(dec_ctx* ctx, int inst, double* out3_host) {
-  const int64_t n = ctx->n;
-  cudaStream_t s = ctx->stream;
-  const unsigned G = (unsigned)ctx->grid_vec;
-  const int ts = ctx->n_sets > 1 ? inst : 0;
-  double* T = ctx->t64.p;  // scratch
-  ctx->launches += 2;
-  form_T_kernel<<<G, kBlock, 0, s>>>(n, ctx->u.p + (int64_t)inst * n,
-                                     ctx->T0.p + (int64_t)ts * n, ctx->tag.p, T);
-  k_eff_kernel<<<G, kBlock, 0, s>>>(n, ctx->rowptr.p, ctx->col.p, ctx->eid.p,
-                                    ctx->dpos.p, ctx->tag.p, ctx->xyz.p, ctx->w.p,
-                                    ctx->first_cut.p, ctx->n_scales > 1 ? inst : 0, T,
-                                    ctx->out3.p + 3 * (int64_t)inst, ctx->partial.p,
-                                    ctx->ticket.p);
-  DEC_TRY(cudaGetLastError());
-  DEC_TRY(cudaMemcpyAsync(out3_host, ctx->out3.p + 3 * (int64_t)inst,
-                          3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  DEC_TRY(cudaStreamSynchronize(s));
-  return DEC_OK;
 }
 
 dec_status form_T(dec_ctx* ctx, int inst, double* T) {
