@@ -55,11 +55,10 @@ __device__ __forceinline__ V3 tri_circumcentre(V3 p, V3 q, V3 r) {
 // Distance, in the disc's plane, from the disc centre to the segment where
 // the plane meets the closed triangle (P0, P1, P2); +inf when the plane misses
 // the triangle or contains it.
-__device__ double crack_rho(V3 P0, V3 P1, V3 P2, V3 c, V3 nrm) {
+// s0..s2 are the signed distances dot(P_i - c, nrm) of the three points.
+__device__ double crack_rho_s(V3 P0, V3 P1, V3 P2, double s0, double s1, double s2, V3 c) {
   V3 P[3] = {P0, P1, P2};
-  double s[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) s[i] = dot(P[i] - c, nrm);
+  const double s[3] = {s0, s1, s2};
   int count = 0;
   V3 A = mk(0, 0, 0), B = mk(0, 0, 0);
   const int ei[3] = {0, 1, 0}, ej[3] = {1, 2, 2};
@@ -198,6 +197,10 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
       // with a relative margin; the cut decision itself stays exact.
       const double RT2 = dot(cT, cT) * (1.0 + 1e-9) + 1e-300;
       const double RT = sqrt(RT2);
+      // Signed distances to the disc plane of the 11 points of the 12 dual
+      // sub-triangles (6 edge midpoints, 4 face circumcentres, c_T) are
+      // computed once per disc; a sub-triangle strictly on one side of the
+      // plane cannot be cut and skips the exact test.
       auto test_disc = [&](int id) {
         const double* dsc = grid.discs + 7 * (int64_t)id;
         V3 dc = mk(dsc[0], dsc[1], dsc[2]);
@@ -211,14 +214,22 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
           const double reach = grid.smax * r * (1.0 + 1e-9);
           if (par2 > reach * reach + 2.0 * reach * RT + RT2) return;
         }
+        const double sT = dot(cTa - dc, dn);
+        double sF[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sF[v] = dot(cF[v] - dc, dn);
 #pragma unroll
         for (int s = 0; s < 6; ++s) {
           if (first[s] == 0) continue;
           V3 me = 0.5 * (X[kEdgeA[s]] + X[kEdgeB[s]]);
+          const double sM = dot(me - dc, dn);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int opp = h == 0 ? kEdgeD[s] : kEdgeC[s];
-            double rho = crack_rho(me, cF[opp], cTa, dc, dn);
+            const double sf = sF[opp];
+            if ((sM > 0.0 && sf > 0.0 && sT > 0.0) || (sM < 0.0 && sf < 0.0 && sT < 0.0))
+              continue;                                   // no crossing: rho = inf
+            const double rho = crack_rho_s(me, cF[opp], cTa, sM, sf, sT, dc);
             for (int st = 0; st < (int)first[s]; ++st)
               if (rho <= grid.scales[st] * r) {
                 first[s] = (uint8_t)st;
@@ -365,6 +376,8 @@ dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k) {
       }
     }
     double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    // cells of twice the largest reach (half: 22 % slower on the cracked
+    // cubes, a tet's box then spans more cells and meets discs again)
     double cell = std::max(2.0 * rmax, ext / 128.0);
     for (int k = 0; k < 3; ++k) {
       g.lo[k] = lo[k];
