@@ -375,7 +375,7 @@ def gpu_arm(args, rank, world):
     return out
 
 
-KERNEL_REV = "r1"
+KERNEL_REV = "r2"
 
 
 def crack_growth_measure(max_steps=600, oracle_steps=3):
