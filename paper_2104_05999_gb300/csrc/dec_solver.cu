@@ -432,12 +432,17 @@ k_eff_batch_kernel(int64_t n, const int32_t* __restrict__ rowptr,
   }
 }
 
+// one warp per value: lane l adds partials l, l + 32, ... and the warp sum
+// combines the lanes in a fixed order
 __global__ void k_eff_batch_sum_kernel(int nblocks, int nvals, const double* __restrict__ partial,
                                        double* __restrict__ out) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvals; v += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nvals;
+       v += (gridDim.x * blockDim.x) >> 5) {
     double s = 0.0;
-    for (int k = 0; k < nblocks; ++k) s += partial[(int64_t)v * nblocks + k];
-    out[v] = s;
+    for (int k = lane; k < nblocks; k += 32) s += partial[(int64_t)v * nblocks + k];
+    s = warp_sum(s);
+    if (lane == 0) out[v] = s;
   }
 }
 
@@ -446,14 +451,15 @@ dec_status k_eff_all(dec_ctx* ctx, double* out3_host) {
   const int B = ctx->B;
   cudaStream_t s = ctx->stream;
   const unsigned G = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)ctx->num_sms * 8 / std::max(1, B / 8 + 1)));
+      1, std::min<int64_t>((n + kBlock - 1) / kBlock,
+                           (int64_t)ctx->num_sms * (B >= 8 ? 1 : 4)));
   DEC_TRY(ctx->kpartial.ensure((size_t)3 * B * G));
   DEC_TRY(ctx->out3.ensure(3 * (size_t)B + 1));
   k_eff_batch_kernel<<<dim3(G, (unsigned)B), kBlock, 0, s>>>(
       n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->xyz.p, ctx->w.p,
       ctx->first_cut.p, ctx->n_scales > 1, ctx->n_sets > 1, ctx->u.p, ctx->T0.p,
       ctx->kpartial.p);
-  k_eff_batch_sum_kernel<<<(unsigned)((3 * B + 127) / 128), 128, 0, s>>>(
+  k_eff_batch_sum_kernel<<<(unsigned)((3 * B + 3) / 4), 128, 0, s>>>(
       (int)G, 3 * B, ctx->kpartial.p, ctx->out3.p);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 2;
