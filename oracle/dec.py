@@ -47,7 +47,7 @@ __all__ = [
     "circumcentre_tri", "hodge_pieces", "hodge_star1", "dual_volumes",
     "crack_rho", "edge_crack_state", "laplacian", "full_laplacian",
     "jacobi", "fsai_factor", "pcg", "k_eff", "rms_error", "solve_path",
-    "crackable_edges", "crack_evolution",
+    "crackable_edges", "crack_evolution", "degenerate_nodes",
 ]
 
 DIRICHLET = 1
@@ -490,6 +490,26 @@ def k_eff(xyz, E, w, T, tags):
     x0 = dirich & (xyz[:, 0] == 0.0)
     x1 = dirich & (xyz[:, 0] == 1.0)
     return out[x0].sum(), -out[x1].sum(), np.sum(w * (T[i] - T[j]) ** 2)
+
+
+def degenerate_nodes(n, E, w, tags):
+    """Cracks can cut nodes off from the Dirichlet faces.  Returns
+    (isolated, islands, island_nodes): free nodes with no conducting edge
+    (identity rows, T = 0), and the components of two or more nodes of the
+    graph of conducting edges (w > 0) that contain no Dirichlet node (their
+    block of L is singular; its right-hand side is zero, so CG from x0 = 0
+    leaves T = 0 there with a preconditioner that keeps the block apart)."""
+    from scipy.sparse.csgraph import connected_components
+    keep = np.asarray(w) > 0.0
+    G = sp.coo_matrix((np.ones(int(keep.sum())), (E[keep, 0], E[keep, 1])),
+                      shape=(n, n))
+    _, lab = connected_components(G, directed=False)
+    size = np.bincount(lab)
+    dirich = np.zeros(len(size), dtype=bool)
+    dirich[lab[np.asarray(tags) == DIRICHLET]] = True
+    isolated = int(np.sum((size == 1) & ~dirich))
+    island = (size >= 2) & ~dirich
+    return isolated, int(island.sum()), int(size[island].sum())
 
 
 # ---------------------------------------------------------------------------

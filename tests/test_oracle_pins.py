@@ -506,3 +506,26 @@ def test_ordered_cracks_equal_cutting_them_at_once():
     with pytest.raises(ValueError):
         O.crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], k=wl.k,
                           rule="order", order=[order[0], order[0]], max_steps=2)
+
+
+def test_degenerate_nodes_counts_isolated_nodes_and_islands():
+    # a 3 x 3 x 3 Kuhn lattice with hand-made cuts: zeroing every edge of the
+    # centre node isolates it; zeroing every edge leaving the pair {centre,
+    # its +y neighbour} except the one between them makes an island of 2
+    wl = make_workload("kuhn9", N=3)
+    E, t2e = O.edge_list(wl.tets)
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e)
+    w = np.where(w > 1e-12, w, 0.0)                 # drop the ~1e-17 diagonals
+    c = 1 + 3 * (1 + 3 * 1)                         # node (1, 1, 1)
+    wi = w.copy()
+    wi[(E[:, 0] == c) | (E[:, 1] == c)] = 0.0
+    assert O.degenerate_nodes(wl.n, E, wi, wl.tags) == (1, 0, 0)
+    d = 1 + 3 * (2 + 3 * 1)                         # node (1, 2, 1), on y = 1
+    pair = {c, d}
+    touch = np.isin(E[:, 0], list(pair)) | np.isin(E[:, 1], list(pair))
+    inside = np.isin(E[:, 0], list(pair)) & np.isin(E[:, 1], list(pair))
+    wp = w.copy()
+    wp[touch & ~inside] = 0.0
+    assert wp[inside].max() > 0.0
+    assert O.degenerate_nodes(wl.n, E, wp, wl.tags) == (0, 1, 2)
+    assert O.degenerate_nodes(wl.n, E, w, wl.tags) == (0, 0, 0)
