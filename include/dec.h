@@ -192,6 +192,17 @@ dec_status dec_solve(dec_ctx* ctx, double rtol, int32_t max_iter, int32_t mode,
  * For T0 = 1 on x = 0 and 0 on x = 1 in the unit cube, k_eff = q_in. */
 dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy);
 
+/* Launch shape the last DEC_MODE_MIXED_BATCHED solve of this context used,
+ * as picked by its autotuner: the first batched solve of a problem size
+ * (nodes, matrix entries) at each instance stride (8, 16, 32, 64) times a
+ * few iterations of every gather variant and keeps the fastest for the
+ * context's later solves of that size.
+ *   gather_entries  host: 0 = gathers into registers, 4 at a time; G > 0 =
+ *                   gathers into shared memory, G entries per round trip.
+ * All variants give bit-identical results.  DEC_ERR_STATE before the first
+ * batched solve.  (No counterpart in the paper: a launch-shape choice.) */
+dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries);
+
 /* crack rules (dec_crack_evolve) */
 enum {
   DEC_CRACK_MAX_FLUX = 0,   /* the face with the largest flux cracks (Sec. 3.3)   */

@@ -52,6 +52,7 @@ SIGNATURES = {
     "dec_solve": [_P, _D, _I32, _I32, _P, _P, _P],
     "dec_k_eff": [_P, _P, _P, _P],
     "dec_crack_evolve": [_P, _I32, _I32, _P, _D, _I32, _I32, _D, _P, _P, _P],
+    "dec_get_batch_variant": [_P, _P],
     "dec_get_sizes": [_P, _P, _P, _P, _P, _P],
     "dec_get_edges": [_P, _P, _P],
     "dec_get_hodge": [_P, _P, _P],
@@ -208,6 +209,13 @@ class Context:
         return st, cracked[:k].copy(), keff[:k].copy()
 
     # ---- getters --------------------------------------------------------
+    def dec_get_batch_variant(self):
+        """Gather entries per round trip the autotuner picked for the last
+        batched solve (0: register gathers)."""
+        v = C.c_int32()
+        self._check(self.lib.dec_get_batch_variant(self.h, C.byref(v)))
+        return v.value
+
     def sizes(self):
         v = [C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()]
         b = C.c_int32()

@@ -346,6 +346,16 @@ dec_status dec_crack_evolve(dec_ctx* ctx, int32_t rule, int32_t max_steps,
   return st;
 }
 
+dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (!gather_entries) return ctx->fail(DEC_ERR_ARG, "get_batch_variant: NULL output");
+  if (ctx->batch_variant_used < 0)
+    return ctx->fail(DEC_ERR_STATE, "get_batch_variant: no batched solve yet");
+  *gather_entries = ctx->batch_variant_used;
+  return DEC_OK;
+}
+
 dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy) {
   if (!ctx) return DEC_ERR_ARG;
   ctx->err.clear();

@@ -158,21 +158,21 @@ __device__ __forceinline__ void set4(float4& v, int j, float x) {
   if (j == 0) v.x = x; else if (j == 1) v.y = x; else if (j == 2) v.z = x; else v.w = x;
 }
 
-// The gathers of the FP32 row products go to shared memory with 16-byte
-// asynchronous copies: registers (64 per thread at 1024 threads per SM) do
-// not bound the gathers in flight, so a row takes ceil(entries / kGU) round
-// trips instead of ceil(entries / 4).  Slot u of thread t is
-// slots[u * 1024 + t] (conflict-free 16-byte accesses); a thread reads only
-// its own slots, so no barrier is needed.
-#ifndef DEC_BATCH_GU
-#define DEC_BATCH_GU 6
-#endif
-#ifndef DEC_BATCH_ASYNC_MIN_BS
-#define DEC_BATCH_ASYNC_MIN_BS 32
-#endif
-constexpr int kAsyncMinBS = DEC_BATCH_ASYNC_MIN_BS;
-constexpr int kGU = DEC_BATCH_GU;
-constexpr int kGatherSmem = kGU * kBBlock * (int)sizeof(float4);
+// The gathers of the FP32 row products can go to shared memory with
+// 16-byte asynchronous copies: registers (64 per thread at 1024 threads per
+// SM) then do not bound the gathers in flight, and a row takes
+// ceil(entries / kGU) round trips instead of ceil(entries / 4).  Slot u of
+// thread t is slots[u * 1024 + t] (conflict-free 16-byte accesses); a thread
+// reads only its own slots, so no barrier is needed.  The shared memory
+// comes out of L1, which costs more than it gains when few threads share a
+// row (8 instances); the autotuner in solve_batched picks the variant.
+// Gather variants of the batched kernel (the autotuner picks one per
+// problem, see solve_batched): 0 = register gathers, 4 at a time; G > 0 =
+// shared-memory gathers, G entries per round trip.
+constexpr int kGatherVariants[] = {0, 4, 6, 8};
+constexpr int kNumGatherVariants = 4;
+template <int GU>
+constexpr int gather_smem() { return GU * kBBlock * (int)sizeof(float4); }
 
 __device__ __forceinline__ float4* gather_slots() {
   extern __shared__ __align__(16) float4 bsm_slots[];
@@ -188,6 +188,7 @@ __device__ __forceinline__ void gather_wait() {
 
 // (L_b x)_i for the four instances 4q..4q+3 of row i (FP32).  The diagonal
 // slot carries w = 0, so it needs no test.
+template <int kGU>
 __device__ __forceinline__ float4 edge_form4_async(const BatchArgs& a, int64_t i, int q,
                                              const int (&st)[kIPT],
                                              const float4* __restrict__ X) {
@@ -309,6 +310,7 @@ __device__ __forceinline__ void edge_form4_64(const BatchArgs& a, int64_t i, int
 
 // FSAI halves (lower: G, upper: G^T) for four instances; per-instance
 // factors (gb) or the shared one (g); gathers as in edge_form4
+template <int kGU>
 __device__ __forceinline__ float4 fsai4_async(const BatchArgs& a, int64_t i, int q, bool lower,
                                         const float4* __restrict__ X) {
   const int BS = a.BS, TPR = BS / kIPT;
@@ -395,17 +397,19 @@ __device__ __forceinline__ float4 fsai4_reg(const BatchArgs& a, int64_t i, int q
   return make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
 
-// Row products of the kernel: shared-memory gathers (ASYNC) or registers
-template <bool ASYNC>
+// Row products of the kernel: shared-memory gathers (GU > 0) or registers.
+// Every variant adds the entries of a row in the same order, so all give
+// bit-identical results.
+template <int GU>
 __device__ __forceinline__ float4 edge_form4(const BatchArgs& a, int64_t i, int q,
                                              const int (&st)[kIPT], const float4* X) {
-  if constexpr (ASYNC) return edge_form4_async(a, i, q, st, X);
+  if constexpr (GU > 0) return edge_form4_async<GU>(a, i, q, st, X);
   else return edge_form4_reg(a, i, q, st, X);
 }
-template <bool ASYNC>
+template <int GU>
 __device__ __forceinline__ float4 fsai4(const BatchArgs& a, int64_t i, int q, bool lower,
                                         const float4* X) {
-  if constexpr (ASYNC) return fsai4_async(a, i, q, lower, X);
+  if constexpr (GU > 0) return fsai4_async<GU>(a, i, q, lower, X);
   else return fsai4_reg(a, i, q, lower, X);
 }
 
@@ -422,7 +426,7 @@ struct Acc2 {
   __device__ __forceinline__ double get() const { return d + (double)f; }
 };
 
-template <bool ASYNC>
+template <int GU>
 __global__ void __launch_bounds__(kBBlock, 1)
 pcg_batched_persistent(BatchArgs a) {
   __shared__ BState S;
@@ -488,13 +492,13 @@ pcg_batched_persistent(BatchArgs a) {
   for (;;) {
     // ---- segment start for the active instances: z = M r, p = z + beta p
     if (any4(S.active))
-      for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4<ASYNC>(a, i, q, true, R);
+      for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4<GU>(a, i, q, true, R);
     if (!bgrid_sync(a.bar, err)) return;
     {
       Acc2 acc[kIPT];
       if (any4(S.active))
         for (int64_t i = row0; i < n; i += rstep) {
-          const float4 zi = fsai4<ASYNC>(a, i, q, false, T);
+          const float4 zi = fsai4<GU>(a, i, q, false, T);
           Z[i * TPR + q] = zi;
           const float4 ri = R[i * TPR + q];
 #pragma unroll
@@ -531,7 +535,7 @@ pcg_batched_persistent(BatchArgs a) {
         Acc2 acc[kIPT];
         if (any4(S.iterating))
           for (int64_t i = row0; i < n; i += rstep) {
-            const float4 qi = edge_form4<ASYNC>(a, i, q, st, Pv);
+            const float4 qi = edge_form4<GU>(a, i, q, st, Pv);
             Q[i * TPR + q] = qi;
             const float4 pi = Pv[i * TPR + q];
 #pragma unroll
@@ -591,13 +595,13 @@ pcg_batched_persistent(BatchArgs a) {
       if (S.count == 0) break;
       // preconditioner on the iterating instances
       if (any4(S.iterating))
-        for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4<ASYNC>(a, i, q, true, R);
+        for (int64_t i = row0; i < n; i += rstep) T[i * TPR + q] = fsai4<GU>(a, i, q, true, R);
       if (!bgrid_sync(a.bar, err)) return;
       {
         Acc2 acc[kIPT];
         if (any4(S.iterating))
           for (int64_t i = row0; i < n; i += rstep) {
-            const float4 zi = fsai4<ASYNC>(a, i, q, false, T);
+            const float4 zi = fsai4<GU>(a, i, q, false, T);
             Z[i * TPR + q] = zi;
             const float4 ri = R[i * TPR + q];
 #pragma unroll
@@ -944,18 +948,23 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   cudaStream_t s = ctx->stream;
   const int B = ctx->B, BS = batch_stride(B);
   if (B > kBMax) return ctx->fail(DEC_ERR_LIMIT, "batched solve: more than 64 instances");
-  int coop = 0, per_sm = 0;
+  int coop = 0;
   DEC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
-  // shared-memory gathers pay from 8 threads per row (BS >= 32); with fewer
-  // threads per row the L1 they give up costs more than they gain
-  const bool async = BS >= kAsyncMinBS;
-  const void* kern = async ? (const void*)pcg_batched_persistent<true>
-                           : (const void*)pcg_batched_persistent<false>;
-  const int smem = async ? kGatherSmem : 0;
-  DEC_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  DEC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBBlock, smem));
-  if (!coop || per_sm < 1)
-    return ctx->fail(DEC_ERR_LIMIT, "batched solve: cooperative launch unavailable");
+  if (!coop) return ctx->fail(DEC_ERR_LIMIT, "batched solve: cooperative launch unavailable");
+  const void* kern[kNumGatherVariants] = {
+      (const void*)pcg_batched_persistent<0>, (const void*)pcg_batched_persistent<4>,
+      (const void*)pcg_batched_persistent<6>, (const void*)pcg_batched_persistent<8>};
+  const int smem[kNumGatherVariants] = {0, gather_smem<4>(), gather_smem<6>(), gather_smem<8>()};
+  bool usable[kNumGatherVariants];
+  bool any = false;
+  for (int v = 0; v < kNumGatherVariants; ++v) {
+    int per_sm = 0;
+    DEC_TRY(cudaFuncSetAttribute(kern[v], cudaFuncAttributeMaxDynamicSharedMemorySize, smem[v]));
+    DEC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[v], kBBlock, smem[v]));
+    usable[v] = per_sm >= 1;
+    any = any || usable[v];
+  }
+  if (!any) return ctx->fail(DEC_ERR_LIMIT, "batched solve: cooperative launch unavailable");
   const int grid = ctx->num_sms;
   const size_t nv = (size_t)n * BS;
   for (auto* bf : {&ctx->bx64, &ctx->br64}) DEC_TRY(bf->ensure(nv));
@@ -967,7 +976,6 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   int* status = reinterpret_cast<int*>(ctx->coop.p + 2);
   int* its = reinterpret_cast<int*>(ctx->coop.p + 16);
   double* result = reinterpret_cast<double*>(ctx->coop.p + 16 + kBMax / 2);
-  DEC_TRY(cudaMemsetAsync(ctx->coop.p, 0, sizeof(int64_t) * (16 + 3 * kBMax), s));
   BatchArgs a{};
   a.n = n;
   a.B = B;
@@ -996,8 +1004,58 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   a.seg2 = 1e-4;
   a.max_iter = max_iter;
   void* args[] = {&a};
-  DEC_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kBBlock), args, smem, s));
-  ctx->launches += 1;
+  auto launch = [&](int v, int iters_cap) -> cudaError_t {
+    a.max_iter = iters_cap;
+    cudaError_t e = cudaMemsetAsync(ctx->coop.p, 0, sizeof(int64_t) * (16 + 3 * kBMax), s);
+    if (e == cudaSuccess)
+      e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args, smem[v], s);
+    ctx->launches += 1;
+    return e;
+  };
+  // Autotuner: the first batched solve of a problem size at this instance
+  // stride times kTuneIters FP32 iterations of every gather variant and keeps
+  // the fastest (register gathers won at 8 instances, shared-memory gathers of 6
+  // entries at 64).  All variants give bit-identical results.
+  int slot = 0;
+  while ((8 << slot) < BS) ++slot;
+  // the choice is kept for later solves of a problem of the same size (the
+  // same mesh uploaded again, as a benchmark or a time loop does)
+  const bool same = ctx->batch_tune_key[slot][0] == n && ctx->batch_tune_key[slot][1] == ctx->nnz;
+  int v = same ? ctx->batch_variant[slot] - 1 : -1;
+  if (v < 0) {
+    constexpr int kTuneIters = 8;
+    cudaEvent_t e0, e1;
+    DEC_TRY(cudaEventCreate(&e0));
+    DEC_TRY(cudaEventCreate(&e1));
+    float best = 0.0f;
+    for (int c = 0; c < kNumGatherVariants; ++c) {
+      if (!usable[c]) continue;
+      DEC_TRY(cudaEventRecord(e0, s));
+      DEC_TRY(launch(c, kTuneIters));
+      DEC_TRY(cudaEventRecord(e1, s));
+      DEC_TRY(cudaEventSynchronize(e1));
+      int hs0 = 0;
+      DEC_TRY(cudaMemcpy(&hs0, status, sizeof(int), cudaMemcpyDeviceToHost));
+      if (hs0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return ctx->fail(DEC_ERR_TIMEOUT, "batched solve: a grid barrier timed out");
+      }
+      float ms = 0.0f;
+      DEC_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (v < 0 || ms < best) {
+        best = ms;
+        v = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->batch_variant[slot] = v + 1;
+    ctx->batch_tune_key[slot][0] = n;
+    ctx->batch_tune_key[slot][1] = ctx->nnz;
+  }
+  ctx->batch_variant_used = kGatherVariants[v];
+  DEC_TRY(launch(v, max_iter));
   const unsigned g2 = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((n * B + 255) / 256, (int64_t)ctx->num_sms * 16));
   batch_unpack_kernel<<<g2, 256, 0, s>>>(n, B, BS, ctx->bx64.p, ctx->u.p);

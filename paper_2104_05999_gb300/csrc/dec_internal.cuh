@@ -142,6 +142,9 @@ struct dec_ctx {
   dec::DevBuf<double> bw64, bb, bx64, br64, bpartial;
   dec::DevBuf<uint8_t> bfc;
   dec::DevBuf<int64_t> crack_buf;          // crack growth: block bests, picked edge
+  int batch_variant[4] = {0, 0, 0, 0};     // tuned gather variant + 1 per stride 8..64
+  int64_t batch_tune_key[4][2] = {};       // (n, nnz) each choice was tuned for
+  int batch_variant_used = -1;             // gather entries of the last batched solve
   dec::DevBuf<__nv_bfloat16> bg16, bgb;   // shared factor, per-instance factors
   bool batch_per_instance = false;
   dec::DevBuf<float> bx, br, bz, bp, bq, bt;

@@ -342,3 +342,18 @@ def test_batched_mode_needs_shared_factor(abi, ctx):
     st, _, _ = ctx.dec_solve(1e-10, 1000, abi.DEC_MODE_MIXED_BATCHED,
                              raise_on_error=False)
     assert st == abi.DEC_ERR_STATE
+
+
+def test_batched_autotuner_is_cached_and_does_not_change_results(abi, ctx):
+    wl = make_workload("growth96", N=8, n_discs=5, n_scales=40)
+    with pytest.raises(abi.DecError):
+        ctx.dec_get_batch_variant()                # no batched solve yet
+    res1 = _run(abi, ctx, wl, "fsai_shared", "batched", 1e-10, discs=wl.discs,
+                scales=wl.scales)
+    v1 = ctx.dec_get_batch_variant()
+    assert v1 in (0, 4, 6, 8)
+    T2 = np.zeros_like(res1.T)
+    _, it2, _ = ctx.dec_solve(1e-10, 50000, abi.DEC_MODE_MIXED_BATCHED, T2)
+    assert ctx.dec_get_batch_variant() == v1     # tuned once per mesh and stride
+    assert np.array_equal(res1.T, T2)
+    assert np.array_equal(res1.iters, it2)
