@@ -603,22 +603,39 @@ def solve_path(xyz, tets, tags, T0, k=None, discs=None, scales=None,
     """The whole path for one mesh: edges, *1 (with cracks), L and b,
     preconditioner, PCG per instance, k_eff per instance.
 
-    Instances are the Dirichlet value sets of ``T0`` (shared *1) or, when
-    ``scales`` is given, the crack states (shared T0[0]).
+    Instances are the Dirichlet value sets of ``T0`` (shared *1), or, when
+    ``scales`` is given, the crack states (shared T0[0]), or, when ``k`` is a
+    stack of per-tet fields [F, m], the conductivity fields (Sec. 1: many
+    material fields on one mesh; shared T0[0] and cracks).
     """
     n = len(xyz)
     E, t2e = edge_list(tets)
-    w0 = hodge_star1(xyz, tets, E, t2e, k)
     T0 = np.atleast_2d(T0)
     first = None
     if discs is not None and len(discs):
         first = edge_crack_state(xyz, tets, E, t2e, discs, scales)
+    if k is not None and np.ndim(k) == 2:
+        if scales is not None:
+            raise ValueError("conductivity fields and crack states at once")
+        inst = []
+        for kf in np.asarray(k):
+            wf = hodge_star1(xyz, tets, E, t2e, kf)
+            inst.append((wf if first is None else np.where(first == 0, 0.0, wf), T0[0]))
+        w0 = hodge_star1(xyz, tets, E, t2e, np.asarray(k)[0])
+        return _solve_instances(xyz, tets, tags, E, t2e, w0, first, inst, precond, rtol)
+    w0 = hodge_star1(xyz, tets, E, t2e, k)
     if scales is not None:
         inst = [(np.where(first <= b, 0.0, w0), T0[0])
                 for b in range(len(scales))]
     else:
         w = w0 if first is None else np.where(first == 0, 0.0, w0)
         inst = [(w, T0[s]) for s in range(T0.shape[0])]
+    return _solve_instances(xyz, tets, tags, E, t2e, w0, first, inst, precond, rtol)
+
+
+def _solve_instances(xyz, tets, tags, E, t2e, w0, first, inst, precond, rtol):
+    """PCG and k_eff for each (*1, T0) instance of solve_path."""
+    n = len(xyz)
     out = dict(E=E, t2e=t2e, w0=w0, first_cut=first, T=[], iters=[],
                relres=[], q_in=[], q_out=[], energy=[], w=[], L=[], b=[])
     dirich = np.asarray(tags) == DIRICHLET

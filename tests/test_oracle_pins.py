@@ -529,3 +529,26 @@ def test_degenerate_nodes_counts_isolated_nodes_and_islands():
     assert wp[inside].max() > 0.0
     assert O.degenerate_nodes(wl.n, E, wp, wl.tags) == (0, 1, 2)
     assert O.degenerate_nodes(wl.n, E, w, wl.tags) == (0, 0, 0)
+
+
+def test_conductivity_fields_as_instances():
+    # Sec. 1: many material fields on one mesh.  Scaling every conductivity
+    # by c scales L and b by c: T is unchanged and k_eff scales by c; each
+    # field obeys the Dirichlet-principle bound with the trial field 1 - x
+    wl = make_workload("lognormal64", N=5)
+    c = np.array([1.0, 2.5, 0.4])
+    fields = c[:, None] * wl.k[None, :]
+    out = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=fields, precond="fsai",
+                       rtol=1e-13)
+    q = np.array(out["q_in"])
+    np.testing.assert_allclose(q / q[0], c, rtol=1e-11)
+    for f in range(3):
+        np.testing.assert_allclose(out["T"][f], out["T"][0], rtol=0, atol=1e-11)
+        E, w = out["E"], out["w"][f]
+        dx = wl.xyz[E[:, 1], 0] - wl.xyz[E[:, 0], 0]
+        assert q[f] <= np.sum(w * dx ** 2) * (1 + 1e-12)
+    single = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=fields[1],
+                          precond="fsai", rtol=1e-13)
+    assert single["q_in"][0] == pytest.approx(q[1], rel=1e-12)
+    with pytest.raises(ValueError):
+        O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=fields, scales=[1.0, 2.0])
