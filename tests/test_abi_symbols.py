@@ -48,3 +48,39 @@ def test_binding_refuses_wrong_dtypes():
         _ptr(np.zeros(3, dtype=np.float32), np.float64)
     with pytest.raises(TypeError):
         _ptr(np.zeros((3, 4), dtype=np.float64)[:, 1], np.float64)
+
+
+def _prototypes():
+    src = open(os.path.join(ROOT, "include", "dec.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(dec_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+        params = " ".join(params.split())
+        out[name] = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+    return out
+
+
+def test_binding_argument_types_match_the_header():
+    # pointer <-> c_void_p, int32_t <-> c_int32, int64_t <-> c_int64,
+    # double <-> c_double, int <-> c_int: a wrong width would pass garbage
+    from paper_2104_05999_gb300 import abi
+    protos = _prototypes()
+    assert set(abi.SIGNATURES) <= set(protos)
+    for name, argt in abi.SIGNATURES.items():
+        params = protos[name]
+        assert len(params) == len(argt), name
+        for p, t in zip(params, argt):
+            if "*" in p:
+                assert t is ctypes.c_void_p or issubclass(t, ctypes._Pointer), (name, p, t)
+                continue
+            if p.startswith("int32_t"):
+                want = ctypes.c_int32
+            elif p.startswith("int64_t"):
+                want = ctypes.c_int64
+            elif p.startswith("double"):
+                want = ctypes.c_double
+            elif p.startswith("int "):
+                want = ctypes.c_int
+            else:
+                raise AssertionError(f"{name}: unhandled parameter type {p!r}")
+            assert t is want, (name, p, t)
