@@ -32,6 +32,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MAX_ITER = 20000
+DATA = {
+    "kuhn9": "Kuhn lattice of the unit cube, k = 1",
+    "lognormal64": "jittered-lattice Delaunay cube, lognormal k (sigma 1) per tet",
+    "cracked128": "jittered-lattice Delaunay cube, k = 1, 2000 penny cracks",
+    "growth96": "jittered-lattice Delaunay cube, k = 1, 1500 penny cracks at 64 radius scales",
+    "hetero192": "jittered-lattice Delaunay cube, lognormal k (sigma 1.5), 5000 penny cracks, "
+                 "8 Dirichlet value sets",
+}
 METRIC = "PCG time to rel-res 1e-10 & SpMV HBM GB/s: mixed/batched vs FP64, 1 GB300"
 L2_FLUSH = 512 << 20
 
@@ -332,8 +340,9 @@ def gpu_arm(args, rank, world):
         "metric": METRIC, "value": round(ms, 4), "unit": "ms",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 4), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded jittered-lattice Delaunay mesh, lognormal k)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if want == "fp64" else "f32 (bf16 FSAI values; f64 residual and k_eff)",
+        "data": "synthetic, seeded: " + DATA.get(wl.name.split("@")[0], "jittered-lattice Delaunay cube"),
         "config": {"workload": wl.name, "n_nodes": n, "n_tets": m,
                    "n_edges": ne, "nnz": nnz, "instances": B,
                    "precond": wl.precond,
