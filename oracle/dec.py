@@ -17,6 +17,8 @@ Section map
   Sec. 2.3 / Sec. 3.1 (Krylov solve to rel. tolerance 1e-10) -> pcg
   Sec. 2.5 (effective conductivity = flux through a Dirichlet face) -> k_eff
   Sec. 3.1 (Eq. 14, volume-weighted RMS error over tets) -> rms_error
+  Sec. 2.3 (Eq. 11-13, the tet-centred mixed system, flux block
+           eliminated) and Sec. 3.1 (the 1e-8 Hodge limiter) -> tet_centred_solve
   Sec. 2.5, 3.3, 3.4 (crack growth: the max-flux face or a random face
            cracks at each step, k_eff after each) -> crackable_edges,
            crack_evolution
@@ -48,6 +50,7 @@ __all__ = [
     "crack_rho", "edge_crack_state", "laplacian", "full_laplacian",
     "jacobi", "fsai_factor", "pcg", "k_eff", "rms_error", "solve_path",
     "crackable_edges", "crack_evolution", "degenerate_nodes",
+    "tet_centred_solve",
 ]
 
 DIRICHLET = 1
@@ -588,6 +591,90 @@ def crack_evolution(xyz, tets, tags, T0, k=None, rule="max_flux",
             break
     return dict(cracked=np.array(cracked, dtype=np.int64), k_eff=np.array(keff),
                 k_eff0=k0, T=T, w=wc, E=E)
+
+
+# ---------------------------------------------------------------------------
+# The paper's own tet-centred form (Sec. 2.3, Eq. 11-13), reduced
+# ---------------------------------------------------------------------------
+
+def tet_centred_solve(xyz, tets, tags, T0, kappa=1.0, limiter=1e-8,
+                      cracked_faces=None):
+    """The mixed system of Eq. 11 (flux per face, potential per tet) with the
+    flux block eliminated, as the paper's Schur-complement solve does: the
+    flux block (1/kappa) *2 is diagonal, so the potentials alpha (one per tet,
+    at its circumcentre) solve the two-point operator
+
+      sum over faces f of w_f (alpha_T - alpha_T'),   w_f = kappa / *2_f,
+
+    with *2_f = l_f / |f|: the signed circumcentric dual edge length over the
+    face area.  Interior face: l_f = h_T + h_T', the signed distances of the
+    two circumcentres to the face (both project onto the face circumcentre,
+    so the dual edge is normal to it).  Boundary face: the incomplete dual
+    edge h_T.  Dirichlet faces (all three nodes Dirichlet) contribute
+    w_f (alpha_T - T0_f), T0_f the mean of their nodes' values; other
+    boundary faces carry no flux (Neumann f0 = 0).  Sec. 3.1 limits Hodge
+    entries from near-zero dual edges to 1e-8: *2_f = max(*2_f, limiter)
+    (limiter=None: no limit).  Cracked faces get w_f = 0 (Sec. 2.5).
+
+    Returns dict(alpha, q_in, q_out, faces, t2f, ell, area, w, limited):
+    q_in the heat entering through the Dirichlet faces on x = 0, q_out the
+    heat leaving through those on x = 1 (k_eff for the unit cube).
+    """
+    xyz = np.asarray(xyz, dtype=np.float64)
+    t = np.asarray(tets, dtype=np.int64)
+    m = len(t)
+    tags = np.asarray(tags)
+    T0 = np.asarray(T0, dtype=np.float64).reshape(-1)
+    opp = ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2))      # face opposite vertex v
+    tri = np.stack([np.sort(t[:, list(o)], axis=1) for o in opp], axis=1)   # [m, 4, 3]
+    faces, inv = np.unique(tri.reshape(-1, 3), axis=0, return_inverse=True)
+    t2f = inv.reshape(m, 4)
+    nf = len(faces)
+    X = xyz[t]
+    cT = circumcentre_tet(X)
+    h = np.zeros((m, 4))
+    for v, o in enumerate(opp):
+        a, b, c = X[:, o[0]], X[:, o[1]], X[:, o[2]]
+        nrm = np.cross(b - a, c - a)
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        outward = np.sign(np.einsum("ij,ij->i", a - X[:, v], nrm))
+        h[:, v] = np.einsum("ij,ij->i", a - cT, nrm) * outward
+    ell = np.bincount(t2f.reshape(-1), weights=h.reshape(-1), minlength=nf)
+    count = np.bincount(t2f.reshape(-1), minlength=nf)
+    P = xyz[faces]
+    area = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+    star = ell / area
+    limited = 0
+    if limiter is not None:
+        limited = int(np.sum(star < limiter))
+        star = np.maximum(star, limiter)
+    w = kappa / star
+    if cracked_faces is not None:
+        w[np.asarray(cracked_faces, dtype=np.int64)] = 0.0
+    # the tets of each face
+    owner = np.full((nf, 2), -1, dtype=np.int64)
+    slot = np.zeros(nf, dtype=np.int64)
+    for T_, f in zip(np.repeat(np.arange(m), 4), t2f.reshape(-1)):
+        owner[f, slot[f]] = T_
+        slot[f] += 1
+    inner = count == 2
+    dface = (count == 1) & (tags[faces] == DIRICHLET).all(axis=1)
+    T0f = T0[faces].mean(axis=1)
+    i1, i2, wi = owner[inner, 0], owner[inner, 1], w[inner]
+    rows = np.concatenate([i1, i2, i1, i2, owner[dface, 0]])
+    cols = np.concatenate([i1, i2, i2, i1, owner[dface, 0]])
+    vals = np.concatenate([wi, wi, -wi, -wi, w[dface]])
+    S = sp.csr_matrix((vals, (rows, cols)), shape=(m, m))
+    rhs = np.bincount(owner[dface, 0], weights=w[dface] * T0f[dface], minlength=m)
+    import scipy.sparse.linalg as sla
+    alpha = sla.spsolve(S.tocsc(), rhs)
+    x_face = P[:, :, 0]
+    on0 = dface & (x_face == 0.0).all(axis=1)
+    on1 = dface & (x_face == 1.0).all(axis=1)
+    q_in = np.sum(w[on0] * (T0f[on0] - alpha[owner[on0, 0]]))
+    q_out = np.sum(w[on1] * (alpha[owner[on1, 0]] - T0f[on1]))
+    return dict(alpha=alpha, q_in=q_in, q_out=q_out, faces=faces, t2f=t2f,
+                ell=ell, area=area, w=w, limited=limited, S=S, cT=cT)
 
 
 def rms_error(xyz, tets, T, T_exact):

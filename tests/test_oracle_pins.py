@@ -552,3 +552,32 @@ def test_conductivity_fields_as_instances():
     assert single["q_in"][0] == pytest.approx(q[1], rel=1e-12)
     with pytest.raises(ValueError):
         O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=fields, scales=[1.0, 2.0])
+
+
+# -------------------------------------------- the paper's tet-centred form
+
+def test_tet_form_is_exact_for_a_linear_field_without_the_limiter():
+    # Sec. 3.1: when no Hodge entry is limited the method is exact for the
+    # linear solution: alpha_T = 1 - x(c_T) at every circumcentre, k_eff = 1
+    wl = make_workload("lognormal64", N=6)
+    out = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0], limiter=1e-8)
+    assert out["limited"] == 0
+    np.testing.assert_allclose(out["alpha"], 1.0 - out["cT"][:, 0], atol=1e-11)
+    assert out["q_in"] == pytest.approx(1.0, abs=1e-11)
+    assert out["q_out"] == pytest.approx(1.0, abs=1e-11)
+    S = out["S"]
+    assert abs(S - S.T).sum() == 0.0
+
+
+def test_tet_form_limiter_on_the_kuhn_lattice():
+    # the 6 Kuhn tets of a cube share one circumcentre (the cube centre), so
+    # the 6 faces inside each cube have dual edges of length 0: 6 (N-1)^3
+    # limited entries; the limiter then leaves a small, non-zero error
+    # (Sec. 3.1: the limiter is visible as non-machine-zero error)
+    N = 4
+    wl = make_workload("kuhn9", N=N)
+    out = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0], limiter=1e-8)
+    assert out["limited"] == 6 * (N - 1) ** 3
+    err = np.abs(out["alpha"] - (1.0 - out["cT"][:, 0])).max()
+    assert 1e-10 < err < 1e-5
+    assert out["q_in"] == pytest.approx(1.0, abs=1e-5)
