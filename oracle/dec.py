@@ -50,7 +50,7 @@ __all__ = [
     "crack_rho", "edge_crack_state", "laplacian", "full_laplacian",
     "jacobi", "fsai_factor", "pcg", "k_eff", "rms_error", "solve_path",
     "crackable_edges", "crack_evolution", "degenerate_nodes",
-    "tet_centred_solve",
+    "tet_centred_solve", "tet_crack_evolution",
 ]
 
 DIRICHLET = 1
@@ -674,7 +674,39 @@ def tet_centred_solve(xyz, tets, tags, T0, kappa=1.0, limiter=1e-8,
     q_in = np.sum(w[on0] * (T0f[on0] - alpha[owner[on0, 0]]))
     q_out = np.sum(w[on1] * (alpha[owner[on1, 0]] - T0f[on1]))
     return dict(alpha=alpha, q_in=q_in, q_out=q_out, faces=faces, t2f=t2f,
-                ell=ell, area=area, w=w, limited=limited, S=S, cT=cT)
+                ell=ell, area=area, w=w, limited=limited, S=S, cT=cT,
+                owner=owner, interior=inner, dirichlet=dface)
+
+
+def tet_crack_evolution(xyz, tets, tags, T0, max_steps=100000, k_stop=1e-9,
+                        limiter=1e-8):
+    """Sec. 3.3 in the paper's own form: after each solve the interior face
+    with the largest flux |w_f (alpha_T - alpha_T')| cracks (w_f = 0; the
+    smallest face id wins a tie), until k_eff <= k_stop * k_eff(uncracked).
+    Returns dict(cracked, k_eff, k_eff0, damage) with damage = cracked /
+    interior faces (the paper's count-based damage parameter D_n)."""
+    out = tet_centred_solve(xyz, tets, tags, T0, limiter=limiter)
+    owner, inner = out["owner"], out["interior"]
+    k0 = out["q_in"]
+    cracked, keff = [], []
+    is_cracked = np.zeros(len(out["faces"]), dtype=bool)
+    for _ in range(max_steps):
+        live = np.flatnonzero(inner & ~is_cracked)
+        if len(live) == 0:
+            break
+        a = out["alpha"]
+        flux = np.abs(out["w"][live] * (a[owner[live, 0]] - a[owner[live, 1]]))
+        f = int(live[np.argmax(flux)])
+        is_cracked[f] = True
+        cracked.append(f)
+        out = tet_centred_solve(xyz, tets, tags, T0, limiter=limiter,
+                                cracked_faces=np.flatnonzero(is_cracked))
+        keff.append(out["q_in"])
+        if out["q_in"] <= k_stop * k0:
+            break
+    return dict(cracked=np.array(cracked, dtype=np.int64), k_eff=np.array(keff),
+                k_eff0=k0, damage=len(cracked) / max(1, int(inner.sum())),
+                faces=out["faces"], owner=owner, interior=inner)
 
 
 def rms_error(xyz, tets, T, T_exact):

@@ -581,3 +581,29 @@ def test_tet_form_limiter_on_the_kuhn_lattice():
     err = np.abs(out["alpha"] - (1.0 - out["cT"][:, 0])).max()
     assert 1e-10 < err < 1e-5
     assert out["q_in"] == pytest.approx(1.0, abs=1e-5)
+
+
+def test_tet_form_max_flux_cracking_ends_at_separation():
+    # Sec. 3.3 in the tet form: k_eff never rises as faces crack, and the
+    # loop ends exactly when no chain of uncracked interior faces links a
+    # tet on x = 0 to a tet on x = 1
+    from scipy.sparse.csgraph import connected_components
+    wl = make_workload("lognormal64", N=5)
+    out = O.tet_crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0])
+    k = out["k_eff"]
+    assert (np.diff(k) <= 1e-12 * out["k_eff0"]).all()
+    assert k[-1] <= 1e-9 * out["k_eff0"] < k[-2]
+    m = len(wl.tets)
+    owner, inner = out["owner"], out["interior"]
+
+    def linked(cracked):
+        keep = inner.copy()
+        keep[cracked] = False
+        G = sp.coo_matrix((np.ones(keep.sum()), (owner[keep, 0], owner[keep, 1])),
+                          shape=(m, m))
+        _, lab = connected_components(G, directed=False)
+        x = wl.xyz[:, 0]
+        on = lambda v: np.flatnonzero((x[wl.tets] == v).sum(axis=1) == 3)  # noqa: E731
+        return bool(np.intersect1d(lab[on(0.0)], lab[on(1.0)]).size)
+    assert not linked(out["cracked"])
+    assert linked(out["cracked"][:-1])
