@@ -612,7 +612,9 @@ def tet_centred_solve(xyz, tets, tags, T0, kappa=1.0, limiter=1e-8,
     so the dual edge is normal to it).  Boundary face: the incomplete dual
     edge h_T.  Dirichlet faces (all three nodes Dirichlet) contribute
     w_f (alpha_T - T0_f), T0_f the mean of their nodes' values; other
-    boundary faces carry no flux (Neumann f0 = 0).  Sec. 3.1 limits Hodge
+    boundary faces carry no flux (Neumann f0 = 0).  A group of tets that
+    cracks cut off from every Dirichlet face keeps alpha = 0 (its block is
+    singular with zero right-hand side; one tet of it is anchored).  Sec. 3.1 limits Hodge
     entries from near-zero dual edges to 1e-8: *2_f = max(*2_f, limiter)
     (limiter=None: no limit).  Cracked faces get w_f = 0 (Sec. 2.5).
 
@@ -664,6 +666,22 @@ def tet_centred_solve(xyz, tets, tags, T0, kappa=1.0, limiter=1e-8,
     rows = np.concatenate([i1, i2, i1, i2, owner[dface, 0]])
     cols = np.concatenate([i1, i2, i2, i1, owner[dface, 0]])
     vals = np.concatenate([wi, wi, -wi, -wi, w[dface]])
+    # components of tets joined by conducting faces that touch no Dirichlet
+    # face (cut off by cracks) have a singular block with zero right-hand
+    # side; one anchored tet per component fixes their potential at 0
+    from scipy.sparse.csgraph import connected_components
+    cond = wi > 0.0
+    Gc = sp.coo_matrix((np.ones(int(cond.sum())), (i1[cond], i2[cond])), shape=(m, m))
+    _, lab = connected_components(Gc, directed=False)
+    anchored = np.ones(lab.max() + 1, dtype=bool)
+    anchored[lab[owner[dface & (w > 0.0), 0]]] = False
+    first = np.full(lab.max() + 1, -1, dtype=np.int64)
+    for T_ in range(m - 1, -1, -1):
+        first[lab[T_]] = T_
+    anchor = first[anchored]
+    rows = np.concatenate([rows, anchor])
+    cols = np.concatenate([cols, anchor])
+    vals = np.concatenate([vals, np.ones(len(anchor))])
     S = sp.csr_matrix((vals, (rows, cols)), shape=(m, m))
     rhs = np.bincount(owner[dface, 0], weights=w[dface] * T0f[dface], minlength=m)
     import scipy.sparse.linalg as sla
@@ -679,10 +697,12 @@ def tet_centred_solve(xyz, tets, tags, T0, kappa=1.0, limiter=1e-8,
 
 
 def tet_crack_evolution(xyz, tets, tags, T0, max_steps=100000, k_stop=1e-9,
-                        limiter=1e-8):
+                        limiter=1e-8, order=None):
     """Sec. 3.3 in the paper's own form: after each solve the interior face
     with the largest flux |w_f (alpha_T - alpha_T')| cracks (w_f = 0; the
-    smallest face id wins a tie), until k_eff <= k_stop * k_eff(uncracked).
+    smallest face id wins a tie), or, with ``order`` (Sec. 3.4, a random
+    sequence of interior faces drawn by the caller), face order[s] cracks at
+    step s; until k_eff <= k_stop * k_eff(uncracked).
     Returns dict(cracked, k_eff, k_eff0, damage) with damage = cracked /
     interior faces (the paper's count-based damage parameter D_n)."""
     out = tet_centred_solve(xyz, tets, tags, T0, limiter=limiter)
@@ -694,9 +714,16 @@ def tet_crack_evolution(xyz, tets, tags, T0, max_steps=100000, k_stop=1e-9,
         live = np.flatnonzero(inner & ~is_cracked)
         if len(live) == 0:
             break
-        a = out["alpha"]
-        flux = np.abs(out["w"][live] * (a[owner[live, 0]] - a[owner[live, 1]]))
-        f = int(live[np.argmax(flux)])
+        if order is not None:
+            if len(cracked) >= len(order):
+                break
+            f = int(order[len(cracked)])
+            if not inner[f] or is_cracked[f]:
+                raise ValueError(f"order[{len(cracked)}] = {f} is not an uncracked interior face")
+        else:
+            a = out["alpha"]
+            flux = np.abs(out["w"][live] * (a[owner[live, 0]] - a[owner[live, 1]]))
+            f = int(live[np.argmax(flux)])
         is_cracked[f] = True
         cracked.append(f)
         out = tet_centred_solve(xyz, tets, tags, T0, limiter=limiter,

@@ -607,3 +607,18 @@ def test_tet_form_max_flux_cracking_ends_at_separation():
         return bool(np.intersect1d(lab[on(0.0)], lab[on(1.0)]).size)
     assert not linked(out["cracked"])
     assert linked(out["cracked"][:-1])
+
+
+def test_tet_form_cut_off_tets_keep_zero_potential():
+    # cracking the four faces of an interior tet cuts it off: its block is
+    # singular with zero right-hand side and its potential stays 0; the rest
+    # of the solution is finite and the cube still conducts
+    wl = make_workload("lognormal64", N=5)
+    base = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0])
+    inner = base["interior"]
+    t2f = base["t2f"]
+    T = int(np.flatnonzero(inner[t2f].all(axis=1))[0])   # a tet with 4 interior faces
+    out = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0], cracked_faces=t2f[T])
+    assert out["alpha"][T] == 0.0
+    assert np.isfinite(out["alpha"]).all()
+    assert 0.0 < out["q_in"] <= base["q_in"] * (1 + 1e-12)
