@@ -622,3 +622,14 @@ def test_tet_form_cut_off_tets_keep_zero_potential():
     assert out["alpha"][T] == 0.0
     assert np.isfinite(out["alpha"]).all()
     assert 0.0 < out["q_in"] <= base["q_in"] * (1 + 1e-12)
+
+
+def test_tet_form_random_cracking_separates_near_the_papers_damage():
+    # Sec. 3.4 reports that random face cracking makes the cube
+    # non-conductive at a damage of about 0.55 (its 44,879-face mesh, 100
+    # paths); a random path on a small mesh lands in the same range
+    wl = make_workload("lognormal64", N=6)
+    base = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0])
+    order = np.random.default_rng(100).permutation(np.flatnonzero(base["interior"]))
+    out = O.tet_crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], order=order)
+    assert 0.4 < out["damage"] < 0.75
