@@ -50,7 +50,7 @@ __all__ = [
     "crack_rho", "edge_crack_state", "laplacian", "full_laplacian",
     "jacobi", "fsai_factor", "pcg", "k_eff", "rms_error", "solve_path",
     "crackable_edges", "crack_evolution", "degenerate_nodes",
-    "tet_centred_solve", "tet_crack_evolution",
+    "tet_centred_solve", "tet_crack_evolution", "whitney_flux",
 ]
 
 DIRICHLET = 1
@@ -598,7 +598,7 @@ def crack_evolution(xyz, tets, tags, T0, k=None, rule="max_flux",
 # ---------------------------------------------------------------------------
 
 def tet_centred_solve(xyz, tets, tags, T0, kappa=1.0, limiter=1e-8,
-                      cracked_faces=None):
+                      cracked_faces=None, face_flux=None):
     """The mixed system of Eq. 11 (flux per face, potential per tet) with the
     flux block eliminated, as the paper's Schur-complement solve does: the
     flux block (1/kappa) *2 is diagonal, so the potentials alpha (one per tet,
@@ -612,7 +612,8 @@ def tet_centred_solve(xyz, tets, tags, T0, kappa=1.0, limiter=1e-8,
     so the dual edge is normal to it).  Boundary face: the incomplete dual
     edge h_T.  Dirichlet faces (all three nodes Dirichlet) contribute
     w_f (alpha_T - T0_f), T0_f the mean of their nodes' values; other
-    boundary faces carry no flux (Neumann f0 = 0).  A group of tets that
+    boundary faces carry the flux ``face_flux[f]`` (Eq. 13: the Neumann data
+    f0 integrated over the face, outward; None: 0).  A group of tets that
     cracks cut off from every Dirichlet face keeps alpha = 0 (its block is
     singular with zero right-hand side; one tet of it is anchored).  Sec. 3.1 limits Hodge
     entries from near-zero dual edges to 1e-8: *2_f = max(*2_f, limiter)
@@ -684,6 +685,10 @@ def tet_centred_solve(xyz, tets, tags, T0, kappa=1.0, limiter=1e-8,
     vals = np.concatenate([vals, np.ones(len(anchor))])
     S = sp.csr_matrix((vals, (rows, cols)), shape=(m, m))
     rhs = np.bincount(owner[dface, 0], weights=w[dface] * T0f[dface], minlength=m)
+    if face_flux is not None:
+        nface = (count == 1) & ~dface
+        rhs -= np.bincount(owner[nface, 0], weights=np.asarray(face_flux)[nface],
+                           minlength=m)
     import scipy.sparse.linalg as sla
     alpha = sla.spsolve(S.tocsc(), rhs)
     x_face = P[:, :, 0]
@@ -691,9 +696,39 @@ def tet_centred_solve(xyz, tets, tags, T0, kappa=1.0, limiter=1e-8,
     on1 = dface & (x_face == 1.0).all(axis=1)
     q_in = np.sum(w[on0] * (T0f[on0] - alpha[owner[on0, 0]]))
     q_out = np.sum(w[on1] * (alpha[owner[on1, 0]] - T0f[on1]))
+    bflux = np.zeros(nf)          # outward flux through each boundary face
+    bflux[dface] = w[dface] * (alpha[owner[dface, 0]] - T0f[dface])
+    if face_flux is not None:
+        nface = (count == 1) & ~dface
+        bflux[nface] = np.asarray(face_flux)[nface]
     return dict(alpha=alpha, q_in=q_in, q_out=q_out, faces=faces, t2f=t2f,
                 ell=ell, area=area, w=w, limited=limited, S=S, cT=cT,
-                owner=owner, interior=inner, dirichlet=dface)
+                owner=owner, interior=inner, dirichlet=dface, boundary_flux=bflux)
+
+
+def whitney_flux(xyz, tets, out):
+    """Flux vector at each tet's barycentre from its face fluxes (Whitney
+    2-form interpolation, the paper's vector output at cell barycentres):
+    v = sum_i phi_i (b - x_i) / (3 V), phi_i the outward flux through the
+    face opposite vertex i.  Face fluxes come from a tet_centred_solve
+    result: w_f (alpha_T - alpha_T') across interior faces and its
+    ``boundary_flux`` (Dirichlet faces: w_f (alpha_T - T0_f); Neumann faces:
+    the prescribed flux) through boundary faces.  Whitney 2-forms reproduce
+    a constant flux field exactly."""
+    t = np.asarray(tets, dtype=np.int64)
+    X = xyz[t]
+    V = tet_volumes(xyz, t)
+    b = X.mean(axis=1)
+    owner, w, alpha = out["owner"], out["w"], out["alpha"]
+    t2f = out["t2f"]
+    v = np.zeros((len(t), 3))
+    for i in range(4):
+        f = t2f[:, i]
+        other = np.where(owner[f, 0] == np.arange(len(t)), owner[f, 1], owner[f, 0])
+        phi = np.where(other >= 0, w[f] * (alpha - alpha[np.maximum(other, 0)]),
+                       out["boundary_flux"][f])
+        v += phi[:, None] * (b - X[:, i]) / (3.0 * V[:, None])
+    return v
 
 
 def tet_crack_evolution(xyz, tets, tags, T0, max_steps=100000, k_stop=1e-9,

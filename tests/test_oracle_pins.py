@@ -633,3 +633,24 @@ def test_tet_form_random_cracking_separates_near_the_papers_damage():
     order = np.random.default_rng(100).permutation(np.flatnonzero(base["interior"]))
     out = O.tet_crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], order=order)
     assert 0.4 < out["damage"] < 0.75
+
+
+def test_tet_form_neumann_flux_and_whitney_output():
+    # Eq. 13: with x = 1 a Neumann face carrying the outflow of the linear
+    # field (unit flux density, i.e. |f| through each face), the linear
+    # field is still the solution; Whitney 2-forms turn its face fluxes back
+    # into the constant flux vector (1, 0, 0) at every barycentre
+    wl = make_workload("lognormal64", N=6)
+    tags = wl.tags.copy()
+    tags[wl.xyz[:, 0] == 1.0] = 2                      # x = 1 becomes zero-flux...
+    base = O.tet_centred_solve(wl.xyz, wl.tets, tags, wl.T0[0])
+    P = wl.xyz[base["faces"]]
+    on1 = (P[:, :, 0] == 1.0).all(axis=1)
+    flux = np.where(on1, base["area"], 0.0)            # ...with unit outflow density
+    out = O.tet_centred_solve(wl.xyz, wl.tets, tags, wl.T0[0], face_flux=flux)
+    np.testing.assert_allclose(out["alpha"], 1.0 - out["cT"][:, 0], atol=1e-11)
+    assert out["q_in"] == pytest.approx(1.0, abs=1e-11)
+    v = O.whitney_flux(wl.xyz, wl.tets, out)
+    np.testing.assert_allclose(v, np.tile([1.0, 0.0, 0.0], (len(wl.tets), 1)), atol=1e-10)
+    # without the prescribed outflow the x = 1 face is insulated: no flux
+    assert abs(base["q_in"]) < 1e-10
