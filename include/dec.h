@@ -234,7 +234,8 @@ enum {
  * The cracks stay in the context (dec_get_hodge shows them as cut in state
  * 0; dec_k_eff reports the last state).  Errors: DEC_ERR_STATE, DEC_ERR_ARG
  * (also for an order entry that is not a conducting, uncut edge; the steps
- * before it are kept), and the errors of dec_solve. */
+ * before it are kept), and the errors of dec_solve (the crack of the step
+ * whose solve failed stays in the context; *steps counts completed steps). */
 dec_status dec_crack_evolve(dec_ctx* ctx, int32_t rule, int32_t max_steps,
                             const int32_t* order, double rtol, int32_t max_iter, int32_t mode,
                             double k_stop, int32_t* cracked, double* k_eff, int32_t* steps);
