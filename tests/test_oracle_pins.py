@@ -654,3 +654,146 @@ def test_tet_form_neumann_flux_and_whitney_output():
     np.testing.assert_allclose(v, np.tile([1.0, 0.0, 0.0], (len(wl.tets), 1)), atol=1e-10)
     # without the prescribed outflow the x = 1 face is insulated: no flux
     assert abs(base["q_in"]) < 1e-10
+
+
+# ------------------------------------------- crack states and kappa_e, by hand
+
+def test_crack_state_of_one_tet_by_hand():
+    # hand-derived first crack states (tests/golden/right_corner_tet_crack.txt):
+    # the edge takes the smallest rho over its two sub-triangles (Sec. 2.5: a
+    # crack through any part of the dual face insulates it), states are the
+    # first radius factor that reaches rho
+    g = _golden("right_corner_tet_crack.txt")
+    disc = np.array([float(v) for v in g["disc"][0]])
+    scales = np.array([float(v) for v in g["scales"][0]])
+    P = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    T, E, t2e = _single(P)
+    first = O.edge_crack_state(P, T, E, t2e, disc[None, :], scales)
+    index = {tuple(e): i for i, e in enumerate(E.tolist())}
+    assert len(g["edge"]) == len(E)
+    for i, j, _rho, b in g["edge"]:
+        assert first[index[(int(i), int(j))]] == int(b), (i, j)
+    # single state: 0 = cut, 1 = intact
+    one = O.edge_crack_state(P, T, E, t2e, disc[None, :])
+    for i, j, _rho, b in g["edge"]:
+        assert one[index[(int(i), int(j))]] == (0 if int(b) == 0 else 1)
+
+
+def _kuhn_axis_disc_rho(N, x0, yc, zc):
+    """Closed-form crack distances on the Kuhn lattice for a disc in the
+    plane x = x0 (generic: not on a lattice or half-lattice plane) centred at
+    (x0, yc, zc).  The circumcentric dual of the Kuhn lattice is the cubic
+    dual lattice (every Kuhn tet has its cell's centre as circumcentre):
+      * an axis edge's dual face is the square of side h in its bisector
+        plane, centred on the edge midpoint, clipped to the cube;
+      * a face diagonal's dual face has zero area: the segments from its
+        face's centre to the centres of the one or two cells on either side;
+      * a body diagonal's dual is the cell centre alone, which no disc cuts
+        (a point lies in the plane or misses it).
+    The plane x = x0 meets: y-edges and z-edges at lattice index
+    i* = round(x0 / h) (their squares span x0), and the diagonals of the
+    cell faces x = i* h (their dual segments cross x0 at the face centre);
+    nothing else.  Returns {(node a, node b): rho}."""
+    h = 1.0 / (N - 1)
+    i = int(round(x0 / h))
+    assert abs(x0 - i * h) < 0.5 * h and abs(abs(x0 - i * h) - 0.5 * h) > 1e-6
+
+    def nid(a, b, c):
+        return a + N * (b + N * c)
+
+    def gap(v, lo, hi):
+        lo, hi = max(lo, 0.0), min(hi, 1.0)
+        return max(lo - v, 0.0, v - hi)
+
+    rho = {}
+    for j in range(N - 1):              # y-edges (i, j, k) -> (i, j+1, k)
+        for k in range(N):
+            rho[(nid(i, j, k), nid(i, j + 1, k))] = np.hypot(
+                (j + 0.5) * h - yc, gap(zc, (k - 0.5) * h, (k + 0.5) * h))
+    for j in range(N):                  # z-edges (i, j, k) -> (i, j, k+1)
+        for k in range(N - 1):
+            rho[(nid(i, j, k), nid(i, j, k + 1))] = np.hypot(
+                gap(yc, (j - 0.5) * h, (j + 0.5) * h), (k + 0.5) * h - zc)
+    for j in range(N - 1):              # diagonals (i,j,k) -> (i,j+1,k+1)
+        for k in range(N - 1):
+            rho[(nid(i, j, k), nid(i, j + 1, k + 1))] = np.hypot(
+                (j + 0.5) * h - yc, (k + 0.5) * h - zc)
+    return rho
+
+
+def test_crack_states_on_the_kuhn_lattice_closed_form():
+    # two discs normal to x and to z (the second as the first with the axes
+    # permuted), several radius factors: first state per edge = min over
+    # discs of the first factor that reaches the closed-form rho
+    N = 6
+    xyz, tets = kuhn_lattice(N)
+    E, t2e = O.edge_list(tets)
+    scales = np.array([0.3, 0.55, 0.8, 1.0])
+    discs = np.array([[0.37, 0.52, 0.44, 1.0, 0.0, 0.0, 0.31],
+                      [0.29, 0.63, 0.61, 0.0, 0.0, 1.0, 0.26]])
+    index = {tuple(e): q for q, e in enumerate(E.tolist())}
+    expect = np.full(len(E), len(scales))
+    margins = []
+    # disc 0: plane x = 0.37
+    rho0 = _kuhn_axis_disc_rho(N, 0.37, 0.52, 0.44)
+    # disc 1: plane z = 0.61; relabel axes (x, y, z) -> (z, x, y), i.e. solve
+    # the problem for coordinates (z, x, y) and map node ids back
+    rho1p = _kuhn_axis_disc_rho(N, 0.61, 0.29, 0.63)
+
+    def unperm(a):            # id in permuted labels (z, x, y) -> real id
+        zz, xx, yy = a % N, (a // N) % N, a // (N * N)
+        return xx + N * (yy + N * zz)
+
+    rho1 = {tuple(sorted((unperm(a), unperm(b)))): r for (a, b), r in rho1p.items()}
+    for rho, r in ((rho0, 0.31), (rho1, 0.26)):
+        for (a, b), d in rho.items():
+            q = index[(min(a, b), max(a, b))]
+            hit = np.flatnonzero(scales * r >= d)
+            margins.append(np.min(np.abs(scales * r - d)))
+            if hit.size:
+                expect[q] = min(expect[q], hit[0])
+    assert min(margins) > 1e-9            # no ties with the thresholds
+    first = O.edge_crack_state(xyz, tets, E, t2e, discs, scales)
+    assert (expect < len(scales)).sum() > 20
+    assert len(set(expect.tolist())) == len(scales) + 1   # every state occurs
+    np.testing.assert_array_equal(first, expect)
+
+
+def test_conductivity_weights_by_hand():
+    # Sec. 2.1 (conductivity on the dual 2-cell), values derived by hand in
+    # tests/golden/two_tet_conductivity.txt: an unweighted mean of k_T, or
+    # weights by signed part area (parallel conductances), give other values
+    g = _golden("two_tet_conductivity.txt")
+    k = np.array([float(v) for v in g["k"][0]])
+    P = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]])
+    T = np.array([[0, 1, 2, 3], [1, 2, 3, 4]])
+    for t in range(2):
+        if O.tet_volumes(P, T[t:t + 1])[0] < 0:
+            T[t, 2], T[t, 3] = T[t, 3], T[t, 2]
+    E, t2e = O.edge_list(T)
+    w = O.hodge_star1(P, T, E, t2e, k)
+    index = {tuple(e): i for i, e in enumerate(E.tolist())}
+    assert len(g["edge"]) == len(E)
+    for i, j, v in g["edge"]:
+        assert w[index[(int(i), int(j))]] == pytest.approx(float(v), rel=1e-13)
+    # k = 1 gives the purely geometric star: 1/4, 1/12 and 1/24
+    w1 = O.hodge_star1(P, T, E, t2e)
+    assert w1[index[(1, 2)]] == pytest.approx(1.0 / 24.0, rel=1e-13)
+    assert w1[index[(1, 4)]] == pytest.approx(1.0 / 12.0, rel=1e-13)
+
+
+def test_rms_error_closed_forms():
+    # Sec. 3.1, Eq. 14: sqrt(sum_T e_T^2 V_T), e_T the mean of the 4 nodal
+    # errors.  A constant error c gives |c| on the unit cube; an error of 1
+    # at one interior Kuhn node (24 tets of volume h^3/6 around it, e_T =
+    # 1/4) gives sqrt(4 h^3 / 16) = h^1.5 / 2
+    N = 5
+    h = 1.0 / (N - 1)
+    xyz, tets = kuhn_lattice(N)
+    base = np.zeros(len(xyz))
+    assert O.rms_error(xyz, tets, base + 0.3, base) == pytest.approx(0.3, rel=1e-13)
+    node = 2 + N * (2 + N * 2)
+    e = base.copy()
+    e[node] = 1.0
+    assert (tets == node).any(axis=1).sum() == 24
+    assert O.rms_error(xyz, tets, e, base) == pytest.approx(h ** 1.5 / 2, rel=1e-13)
