@@ -6,15 +6,18 @@ laplacian_build (L, b, FSAI factor) -> solve (PCG to rel. residual 1e-10)
 -> k_eff.  Inputs are resident in HBM when a step starts; L2 is flushed
 (a 512 MiB write) between timed steps, outside the timed events.
 
-Prints ONE JSON line (rank 0).  Default workload: the 64^3 jittered
-Delaunay cube with lognormal conductivity (sigma = 1), FP64 PCG with the
-FSAI preconditioner, as specified for that configuration; the mixed
-FP32/BF16 + FP64-refinement solve on the same inputs is reported next to it.
+Prints ONE JSON line (rank 0).  Default workload: the largest single-GPU
+configuration, the 192^3 jittered Delaunay cube with lognormal conductivity
+(sigma = 1.5) and 5000 penny cracks, 8 Dirichlet value sets solved together
+by the batched mixed-precision PCG (FP32 CG, BF16 FSAI factor, FP64 residual
+replacement, one persistent launch); FP64 PCG of each set in turn on the same
+inputs is timed next to it (`other_mode`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 --impl reference times the CPU oracle (the plain FP64 reference of the
-method) on a bounded sample of the same workload, scaled to a full step.
+method) on a complete small instance of the same workload recipe, each phase
+scaled to the full workload by the oracle's own cost law.
 """
 from __future__ import annotations
 
@@ -228,15 +231,22 @@ def gpu_arm(args, rank, world):
                 e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+            if mode == abi.DEC_MODE_MIXED_BATCHED:
+                # device time of the batched kernel's launch in this step
+                # (CUDA events on the context's stream, around the launch)
+                kernel_ms.append(ctx.dec_get_batch_kernel_ms())
         launches = (ctx.dec_get_launch_count() - launches0) / max(steps, 1)
         if bracket:
             sync_ranks(world, dev)
         return times, res, launches
 
+    kernel_ms = []
+
 
     with ClockSampler(dev_id) as clk:
         times, (iters, relres, q_in), launches = timed(mode64, args.steps, args.warmup,
                                                        bracket=True)
+    batch_kernel_ms = list(kernel_ms)
     _log(f"timed steps: {[round(t, 3) for t in times]} ms")
     ms = max_over_ranks(statistics.mean(times), world, dev)
 
@@ -317,11 +327,16 @@ def gpu_arm(args, rank, world):
             BS *= 2
         per_inst_g = wl.scales is not None and len(wl.scales) > 1
         vec = 4 * n * BS
-        roof_bytes = (9 * nnz + 2 * nnz_g * (4 + 2 * (BS if per_inst_g else 1)) +
-                      vec * (2 + 2 + 2 + 9))
-        roof_ms = solve_ms / max(1, int(np.max(iters)))
-        roof_kernel = ("pcg_batched_persistent (per FP32 iteration: edge-form SpMM "
-                       "over %d instances + both FSAI halves + vector updates)" % B)
+        # algorithmic bytes of one launch (the whole batched solve): the
+        # shared structure once per iteration of the slowest instance, the
+        # [n][BS] FP32 vectors per iteration (15 passes) for the mean
+        # iteration count
+        struct = 9 * nnz + 2 * nnz_g * (4 + 2 * (BS if per_inst_g else 1))
+        roof_bytes = (struct * int(np.max(iters)) +
+                      vec * 15 * float(np.mean(iters)))
+        roof_ms = statistics.mean(batch_kernel_ms)
+        roof_kernel = ("pcg_batched_persistent (one launch = the whole solve of "
+                       "%d instances; mean of the timed steps' launches)" % B)
     roof_gbs = roof_bytes / (roof_ms * 1e-3) / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "spmv_f64_traffic.json")
@@ -417,72 +432,148 @@ def crack_growth_measure(max_steps=600, oracle_steps=3):
 
 
 # ------------------------------------------------------------- CPU oracle
-def oracle_sample(wl, m_sample, pcg_iters, target_iters):
-    """Time the oracle's full path on the sub-mesh made of the first
-    ``m_sample`` tets (a slab of the lattice-ordered mesh) and scale every
-    piece linearly to the full mesh; PCG time per iteration is measured over
-    ``pcg_iters`` iterations and scaled to ``target_iters``.  Returns
-    (ms per full step, description)."""
+def oracle_phases(name, N_s):
+    """Run the oracle's whole path, phase by phase, on the complete instance
+    of workload ``name`` at lattice size ``N_s`` (same recipe: jitter, k,
+    discs scaled to the lattice, every Dirichlet set or crack state solved to
+    the workload's tolerance).  Returns the small instance's counts and the
+    seconds of each phase."""
     import oracle as O
-    tets = wl.tets[:m_sample]
-    used = np.unique(tets)
-    remap = -np.ones(wl.n, dtype=np.int64)
-    remap[used] = np.arange(len(used))
-    sub_tets = remap[tets].astype(np.int32)
-    xyz = wl.xyz[used]
-    tags = wl.tags[used]
-    T0 = wl.T0[0][used]
-    k = None if wl.k is None else wl.k[:m_sample]
-    ns = len(used)
-    t0 = time.perf_counter()
-    E, t2e = O.edge_list(sub_tets)
-    w = O.hodge_star1(xyz, sub_tets, E, t2e, k)
-    L, b, _ = O.laplacian(ns, E, w, tags, T0)
-    t1 = time.perf_counter()
-    if wl.precond == "fsai":
-        G = O.fsai_factor(L)
-        Gt = G.T.tocsr()
-        M = lambda r: Gt @ (G @ r)  # noqa: E731
+    from dec_inputs import make_workload
+    wl = make_workload(name, N=N_s)
+    T0 = np.atleast_2d(wl.T0)
+    t = {}
+    c = time.perf_counter()
+    E, t2e = O.edge_list(wl.tets)
+    t["edges"] = time.perf_counter() - c
+    first = None
+    t["crack_fixed"] = t["crack_discs"] = 0.0
+    if wl.discs is not None:
+        # the crack test's cost has a part per sub-triangle (the dual-face
+        # points) and a part per (sub-triangle, disc) pair: time it without
+        # discs, then with all of them
+        c = time.perf_counter()
+        O.edge_crack_state(wl.xyz, wl.tets, E, t2e, wl.discs[:0], wl.scales)
+        t["crack_fixed"] = time.perf_counter() - c
+        c = time.perf_counter()
+        first = O.edge_crack_state(wl.xyz, wl.tets, E, t2e, wl.discs, wl.scales)
+        t["crack_discs"] = max(0.0, time.perf_counter() - c - t["crack_fixed"])
+    c = time.perf_counter()
+    w0 = O.hodge_star1(wl.xyz, wl.tets, E, t2e, wl.k)
+    t["hodge"] = time.perf_counter() - c
+    if wl.scales is not None:
+        inst = [(np.where(first <= b, 0.0, w0), T0[0]) for b in range(len(wl.scales))]
     else:
-        d = O.jacobi(L)
-        M = lambda r: d * r  # noqa: E731
-    t2 = time.perf_counter()
-    O.pcg(L, b[0], M, rtol=1e-300, max_iter=pcg_iters)
-    t3 = time.perf_counter()
-    Tfull = np.zeros(ns)
-    O.k_eff(xyz, E, w, Tfull, tags)
-    t4 = time.perf_counter()
-    fm = wl.m / m_sample
-    fn = wl.n / ns
-    ms = 1e3 * ((t1 - t0) * fm + (t2 - t1) * fn +
-                (t3 - t2) / pcg_iters * fn * target_iters + (t4 - t3) * fn)
-    desc = (f"oracle (numpy/scipy FP64, 1 thread) on the first {m_sample} of "
-            f"{wl.m} tets ({ns} nodes); assembly and preconditioner setup "
-            f"scaled linearly to the full mesh, {pcg_iters} PCG iterations "
-            f"timed and scaled to {target_iters} iterations on the full mesh")
-    return ms, desc
+        w = w0 if first is None else np.where(first == 0, 0.0, w0)
+        inst = [(w, T0[s]) for s in range(T0.shape[0])]
+    t["laplacian"] = t["precond"] = t["pcg"] = t["k_eff"] = 0.0
+    iters, nnz = [], 0
+    dirich = wl.tags == O.DIRICHLET
+    for w, t0 in inst:
+        c = time.perf_counter()
+        L, b, _ = O.laplacian(wl.n, E, w, wl.tags, t0)
+        t["laplacian"] += time.perf_counter() - c
+        nnz = L.nnz
+        c = time.perf_counter()
+        if wl.precond == "fsai":
+            G = O.fsai_factor(L)
+            Gt = G.T.tocsr()
+            M = lambda r, G=G, Gt=Gt: Gt @ (G @ r)  # noqa: E731
+        else:
+            d = O.jacobi(L)
+            M = lambda r, d=d: d * r  # noqa: E731
+        t["precond"] += time.perf_counter() - c
+        c = time.perf_counter()
+        u, it, _ = O.pcg(L, b[0], M, wl.rtol)
+        t["pcg"] += time.perf_counter() - c
+        iters.append(int(it))
+        c = time.perf_counter()
+        O.k_eff(wl.xyz, E, w, u + np.where(dirich, t0, 0.0), wl.tags)
+        t["k_eff"] += time.perf_counter() - c
+    nd = 0 if wl.discs is None else len(wl.discs)
+    return dict(N=N_s, n=wl.n, m=wl.m, nnz=nnz, nd=nd, inst=len(inst),
+                iters=iters, sec=t)
+
+
+def oracle_scaled(name, small, full):
+    """Scale the oracle's measured phases on the small instance to the full
+    workload by the oracle's own cost laws: edge list, Hodge star, L and
+    preconditioner set-up grow with the number of tets; the crack test has a
+    part per sub-triangle (tets) and a brute force over every (sub-triangle,
+    disc) pair (tets x discs); PCG grows with matrix entries x iterations, and FSAI-PCG
+    iterations on these cubes grow in proportion to the lattice size (about
+    3.8 per lattice spacing on the 16^3, 24^3 and 32^3 instances of the
+    heterogeneous cracked cube).  ``full`` holds N, n, m, nnz, nd (counts
+    of the full workload; m and nnz may come from lattice scaling).
+    Returns (ms per step, description, detail dict)."""
+    sec = small["sec"]
+    fm = full["m"] / small["m"]
+    fcr = fm * (max(full["nd"], 1) / max(small["nd"], 1))
+    fit = (full["N"] - 1) / (small["N"] - 1)
+    fpcg = full["nnz"] / small["nnz"] * fit
+    scaled = {"edges": sec["edges"] * fm, "crack_fixed": sec["crack_fixed"] * fm,
+              "crack_discs": sec["crack_discs"] * fcr,
+              "hodge": sec["hodge"] * fm, "laplacian": sec["laplacian"] * fm,
+              "precond": sec["precond"] * fm, "pcg": sec["pcg"] * fpcg,
+              "k_eff": sec["k_eff"] * fm}
+    ms = 1e3 * sum(scaled.values())
+    # crack_fixed is measured once more inside the full crack test: count it
+    # once
+    measured_ms = 1e3 * (sum(sec.values()) - sec["crack_fixed"])
+    desc = (f"oracle (numpy/scipy FP64, 1 thread), whole path on the complete "
+            f"{name}@{small['N']} instance ({small['n']} nodes, {small['m']} tets, "
+            f"{small['nd']} discs, {small['inst']} instances solved to the "
+            f"workload's tolerance in {min(small['iters'])}-{max(small['iters'])} "
+            f"iterations): {measured_ms:.0f} ms measured; each phase scaled to the "
+            f"full workload by the oracle's cost law (tets; crack test tets x "
+            f"discs; PCG entries x iterations, iterations in proportion to the "
+            f"lattice size)")
+    detail = {"measured_ms": round(measured_ms, 1),
+              "measured_instance": f"{name}@{small['N']}",
+              "measured_phases_ms": {k: round(1e3 * v, 1) for k, v in sec.items()},
+              "scaled_phases_ms": {k: round(1e3 * v, 1) for k, v in scaled.items()},
+              "iterations_measured": small["iters"],
+              "iterations_scaled": int(round(np.mean(small["iters"]) * fit))}
+    return ms, desc, detail
+
+
+def full_counts(name, N, small, exact=None):
+    """Counts of the full workload: exact when the GPU arm has them, else
+    scaled from the small instance by the lattice's cell count."""
+    from dec_inputs.workloads import WORKLOADS
+    N0 = WORKLOADS[name][1] if N is None else N
+    nd0 = WORKLOADS[name][4]
+    if exact is not None:
+        n, m, nnz = exact
+    else:
+        f = ((N0 - 1) / (small["N"] - 1)) ** 3
+        n, m, nnz = N0 ** 3, small["m"] * f, small["nnz"] * f
+    nd = nd0 if N is None else max(1, int(round(nd0 * (N / WORKLOADS[name][1]) ** 3)))
+    return {"N": N0, "n": n, "m": m, "nnz": nnz, "nd": nd if nd0 else 0}
 
 
 def reference_arm(args):
-    from dec_inputs import make_workload
-    wl = make_workload(args.workload, N=args.N)
-    target = args.ref_iters
     times = []
-    desc = ""
+    desc, detail = "", {}
+    N_s = args.ref_N
     for i in range(args.warmup + args.steps):
-        ms, desc = oracle_sample(wl, args.ref_tets, 10, target)
+        small = oracle_phases(args.workload, N_s)
+        full = full_counts(args.workload, args.N, small)
+        ms, desc, detail = oracle_scaled(args.workload, small, full)
         if i >= args.warmup:
             times.append(ms)
     ms = statistics.mean(times)
+    from dec_inputs.workloads import WORKLOADS
+    mode = WORKLOADS[args.workload][10]
     return {
         "metric": METRIC, "value": round(ms, 2), "unit": "ms", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": wl.name, "precond": wl.precond, "mode": "fp64",
-                   "rtol": 1e-10},
+        "config": {"workload": args.workload if args.N is None else f"{args.workload}@{args.N}",
+                   "precond": "fsai", "mode": mode, "rtol": 1e-10},
         "cpu_baseline": {"value": round(ms, 2), "unit": "ms", "cores": 1,
-                         "kind": "oracle", "sample": desc},
+                         "kind": "oracle", "sample": desc, **detail},
         "e2e": {"value": round(ms, 2), "unit": "ms", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -494,17 +585,16 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="lognormal64")
+    ap.add_argument("--workload", default="hetero192")
     # another lattice size of the same workload recipe (small profiling cases)
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--mode", default="auto",
                     choices=["auto", "fp64", "mixed", "mixed_phased", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-tets", type=int, default=60000)
-    # PCG iterations of a full solve of the default workload: the FP64 solve
-    # of the 64^3 lognormal cube to 1e-10 takes 191 (the oracle runs the same
-    # preconditioned CG, so it takes the same count up to rounding)
-    ap.add_argument("--ref-iters", type=int, default=191)
+    # lattice size of the complete small instance the oracle runs: per
+    # reference-arm step, and for the GPU arm's cpu_baseline
+    ap.add_argument("--ref-N", type=int, default=14)
+    ap.add_argument("--baseline-N", type=int, default=24)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -520,12 +610,14 @@ def main():
     out = gpu_arm(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            from dec_inputs import make_workload
-            wl = make_workload(args.workload, N=args.N)
-            ms, desc = oracle_sample(wl, 4 * args.ref_tets, 20, out["iters"])
+            small = oracle_phases(args.workload, args.baseline_N)
+            c = out["config"]
+            full = full_counts(args.workload, args.N, small,
+                               exact=(c["n_nodes"], c["n_tets"], c["nnz"]))
+            ms, desc, detail = oracle_scaled(args.workload, small, full)
             out["cpu_baseline"] = {"value": round(ms, 1), "unit": "ms",
                                    "cores": 1, "kind": "oracle",
-                                   "sample": desc}
+                                   "sample": desc, **detail}
             out["crack_growth"] = crack_growth_measure()
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -203,6 +203,13 @@ dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy);
  * batched solve.  (No counterpart in the paper: a launch-shape choice.) */
 dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries);
 
+/* Device time in ms of the persistent kernel launch of the last successful
+ * DEC_MODE_MIXED_BATCHED solve (the launch that solved every instance, not
+ * the autotuner's trial launches), measured by CUDA events recorded on the
+ * context's stream around that launch.  DEC_ERR_STATE before the first
+ * batched solve.  (No counterpart in the paper: a measurement aid.) */
+dec_status dec_get_batch_kernel_ms(dec_ctx* ctx, double* ms);
+
 /* crack rules (dec_crack_evolve) */
 enum {
   DEC_CRACK_MAX_FLUX = 0,   /* the face with the largest flux cracks (Sec. 3.3)   */
@@ -294,6 +301,25 @@ dec_status dec_time_kernel(dec_ctx* ctx, int32_t kernel, int32_t reps,
 /* Number of CUDA kernels the context has launched since dec_create,
  * counting every kernel node of each replayed CUDA graph. */
 dec_status dec_get_launch_count(const dec_ctx* ctx, int64_t* count);
+
+/* ---- testing aid (no counterpart in the paper) ---- */
+
+/* Run the failure path of the persistent solves without any endless wait.
+ * The persistent kernels (DEC_MODE_MIXED up to 400,000 nodes and
+ * DEC_MODE_MIXED_BATCHED) separate their phases by grid barriers that poll a
+ * counter at most 2^24 times (32-256 ns apart) before the kernel records a
+ * failure, every block leaves at its next barrier and the call returns
+ * DEC_ERR_TIMEOUT.  With this switch on, later persistent launches of the
+ * context use
+ *   spin_limit       polls per barrier wait instead of 2^24 (0: unchanged),
+ *   withhold_block   1: the last block of the grid returns before its first
+ *                    barrier, so the other blocks' wait runs out after
+ *                    spin_limit polls; 0: every block takes part.
+ * Every wait stays bounded; the context remains usable, and the next solve
+ * after dec_set_barrier_test(ctx, 0, 0) starts from scratch.
+ * Errors: DEC_ERR_ARG (NULL context, spin_limit < 0 or >= 2^32,
+ * withhold_block not 0 or 1). */
+dec_status dec_set_barrier_test(dec_ctx* ctx, int64_t spin_limit, int32_t withhold_block);
 
 /* ---- an entry point that allocates no device memory ---- */
 

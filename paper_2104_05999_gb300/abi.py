@@ -53,6 +53,7 @@ SIGNATURES = {
     "dec_k_eff": [_P, _P, _P, _P],
     "dec_crack_evolve": [_P, _I32, _I32, _P, _D, _I32, _I32, _D, _P, _P, _P],
     "dec_get_batch_variant": [_P, _P],
+    "dec_get_batch_kernel_ms": [_P, _P],
     "dec_get_sizes": [_P, _P, _P, _P, _P, _P],
     "dec_get_edges": [_P, _P, _P],
     "dec_get_hodge": [_P, _P, _P],
@@ -60,6 +61,7 @@ SIGNATURES = {
     "dec_get_precond": [_P, _P],
     "dec_time_kernel": [_P, _I32, _I32, _I64, _P],
     "dec_get_launch_count": [_P, _P],
+    "dec_set_barrier_test": [_P, _I64, _I32],
     "dec_k_eff_edges_noalloc": [C.c_int, _P, _P, _I64, _P, _P, _P, _P, _P],
 }
 
@@ -216,6 +218,12 @@ class Context:
         self._check(self.lib.dec_get_batch_variant(self.h, C.byref(v)))
         return v.value
 
+    def dec_get_batch_kernel_ms(self):
+        """Device time (ms) of the last batched solve's persistent launch."""
+        v = C.c_double()
+        self._check(self.lib.dec_get_batch_kernel_ms(self.h, C.byref(v)))
+        return v.value
+
     def sizes(self):
         v = [C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()]
         b = C.c_int32()
@@ -259,6 +267,12 @@ class Context:
         c = C.c_int64()
         self._check(self.lib.dec_get_launch_count(self.h, C.byref(c)))
         return c.value
+
+    def dec_set_barrier_test(self, spin_limit=0, withhold_block=0):
+        """Testing aid: shorter barrier waits and a withheld block in the
+        persistent solves (see dec.h); (0, 0) restores normal operation."""
+        return self._check(self.lib.dec_set_barrier_test(
+            self.h, int(spin_limit), int(withhold_block)))
 
     def dec_time_kernel(self, kernel, reps=20, flush_bytes=512 << 20):
         """Mean duration (ms) of one launch of a solver kernel, cold L2."""

@@ -458,6 +458,25 @@ dec_status dec_time_kernel(dec_ctx* ctx, int32_t kernel, int32_t reps,
   return dec::time_kernel(ctx, kernel, reps, (size_t)flush_bytes, avg_ms);
 }
 
+dec_status dec_get_batch_kernel_ms(dec_ctx* ctx, double* ms) {
+  if (!ctx || !ms) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->batch_kernel_ms < 0.0)
+    return ctx->fail(DEC_ERR_STATE, "get_batch_kernel_ms: no batched solve yet");
+  *ms = ctx->batch_kernel_ms;
+  return DEC_OK;
+}
+
+dec_status dec_set_barrier_test(dec_ctx* ctx, int64_t spin_limit, int32_t withhold_block) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (spin_limit < 0 || spin_limit >= (int64_t(1) << 32) || (withhold_block != 0 && withhold_block != 1))
+    return ctx->fail(DEC_ERR_ARG, "set_barrier_test: spin_limit in [0, 2^32), withhold_block 0 or 1");
+  ctx->test_spin_limit = (unsigned)spin_limit;
+  ctx->test_withhold = (unsigned)withhold_block;
+  return DEC_OK;
+}
+
 dec_status dec_get_launch_count(const dec_ctx* ctx, int64_t* count) {
   if (!ctx || !count) return DEC_ERR_ARG;
   *count = ctx->launches;

@@ -71,10 +71,13 @@ __device__ __forceinline__ bool bgrid_sync(unsigned* bar, int* err) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
+      // bar[2] != 0 replaces the poll limit (the context's barrier test)
+      const unsigned lim = *(volatile unsigned*)(bar + 2);
+      const long limit = lim ? (long)lim : kBSpinLimit;
       long polls = 0;
       unsigned ns = 32;
       while (*gen == g) {
-        if (++polls > kBSpinLimit || *(volatile int*)err) {
+        if (++polls > limit || *(volatile int*)err) {
           atomicExch(err, 1);
           break;
         }
@@ -429,6 +432,9 @@ struct Acc2 {
 template <int GU>
 __global__ void __launch_bounds__(kBBlock, 1)
 pcg_batched_persistent(BatchArgs a) {
+  // barrier test: bar[3] != 0 withholds the last block, so the others'
+  // first barrier wait runs out (DEC_ERR_TIMEOUT)
+  if (*(volatile unsigned*)(a.bar + 3) && blockIdx.x == gridDim.x - 1) return;
   __shared__ BState S;
   __shared__ double sh[kBBlock * kIPT];
   const int BS = a.BS, TPR = BS / kIPT;
@@ -1007,6 +1013,7 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   auto launch = [&](int v, int iters_cap) -> cudaError_t {
     a.max_iter = iters_cap;
     cudaError_t e = cudaMemsetAsync(ctx->coop.p, 0, sizeof(int64_t) * (16 + 3 * kBMax), s);
+    if (e == cudaSuccess) e = write_barrier_test(ctx, bar);
     if (e == cudaSuccess)
       e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args, smem[v], s);
     ctx->launches += 1;
@@ -1055,7 +1062,13 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
     ctx->batch_tune_key[slot][1] = ctx->nnz;
   }
   ctx->batch_variant_used = kGatherVariants[v];
+  // device time of the solve's launch (dec_get_batch_kernel_ms)
+  cudaEvent_t k0, k1;
+  DEC_TRY(cudaEventCreate(&k0));
+  DEC_TRY(cudaEventCreate(&k1));
+  DEC_TRY(cudaEventRecord(k0, s));
   DEC_TRY(launch(v, max_iter));
+  DEC_TRY(cudaEventRecord(k1, s));
   const unsigned g2 = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((n * B + 255) / 256, (int64_t)ctx->num_sms * 16));
   batch_unpack_kernel<<<g2, 256, 0, s>>>(n, B, BS, ctx->bx64.p, ctx->u.p);
@@ -1067,6 +1080,11 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   DEC_TRY(cudaMemcpyAsync(hi, its, sizeof(int) * BS, cudaMemcpyDeviceToHost, s));
   DEC_TRY(cudaMemcpyAsync(hr, result, sizeof(double) * 2 * BS, cudaMemcpyDeviceToHost, s));
   DEC_TRY(cudaStreamSynchronize(s));
+  float kms = 0.0f;
+  DEC_TRY(cudaEventElapsedTime(&kms, k0, k1));
+  cudaEventDestroy(k0);
+  cudaEventDestroy(k1);
+  ctx->batch_kernel_ms = kms;
   if (hs[0]) return ctx->fail(DEC_ERR_TIMEOUT, "batched solve: a grid barrier timed out");
   dec_status st = DEC_OK;
   for (int i = 0; i < B; ++i) {

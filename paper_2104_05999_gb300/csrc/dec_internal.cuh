@@ -87,6 +87,9 @@ struct dec_ctx {
   int grid_vec = 0;     // blocks of the element-wise vector kernels
   int grid_sell = 0;    // blocks of the SELL kernels (one slice per warp)
   int64_t launches = 0;  // kernels launched so far (graph nodes included)
+  // barrier test (dec_set_barrier_test): poll limit and withheld block of
+  // the persistent kernels; 0 = normal operation
+  unsigned test_spin_limit = 0, test_withhold = 0;
 
   // mesh
   dec::DevBuf<double> xyz;
@@ -145,6 +148,7 @@ struct dec_ctx {
   int batch_variant[4] = {0, 0, 0, 0};     // tuned gather variant + 1 per stride 8..64
   int64_t batch_tune_key[4][2] = {};       // (n, nnz) each choice was tuned for
   int batch_variant_used = -1;             // gather entries of the last batched solve
+  double batch_kernel_ms = -1.0;           // device time of its persistent launch
   dec::DevBuf<__nv_bfloat16> bg16, bgb;   // shared factor, per-instance factors
   bool batch_per_instance = false;
   dec::DevBuf<float> bx, br, bz, bp, bq, bt;
@@ -197,6 +201,16 @@ struct dec_ctx {
   } while (0)
 
 namespace dec {
+
+// Words 2 and 3 of a persistent kernel's barrier: the poll limit of every
+// wait (0 = the default) and whether the last block leaves at once.  Written
+// after the barrier is cleared and before the launch, only when the
+// context's barrier test is on.
+inline cudaError_t write_barrier_test(dec_ctx* ctx, unsigned* bar) {
+  if (!ctx->test_spin_limit && !ctx->test_withhold) return cudaSuccess;
+  const unsigned v[2] = {ctx->test_spin_limit, ctx->test_withhold};
+  return cudaMemcpyAsync(bar + 2, v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream);
+}
 
 // ------------------------------------------------------ device helpers
 __device__ __forceinline__ double warp_sum(double v) {

@@ -12,7 +12,9 @@
 //
 // The barrier spins on a generation counter with a bounded number of polls;
 // when the bound is hit the kernel records DEC_ERR_TIMEOUT and every block
-// leaves at its next barrier.
+// leaves at its next barrier.  Words 2 and 3 of the barrier (zero in normal
+// use) let a test shorten the bound and withhold a block, so that this
+// failure path runs without any endless wait.
 #include "dec_kern.cuh"
 
 #include <algorithm>
@@ -57,10 +59,13 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
+      // bar[2] != 0 replaces the poll limit (the context's barrier test)
+      const unsigned lim = *(volatile unsigned*)(bar + 2);
+      const long limit = lim ? (long)lim : kSpinLimit;
       long polls = 0;
       unsigned ns = 32;
       while (*gen == g) {
-        if (++polls > kSpinLimit || *(volatile int*)err) {
+        if (++polls > limit || *(volatile int*)err) {
           atomicExch(err, 1);
           break;
         }
@@ -160,6 +165,9 @@ __device__ __forceinline__ float sell_row2(const SellArg<MT>& A, int64_t s, int 
 template <bool JACOBI>
 __global__ void __launch_bounds__(kPBlock, 1)
 pcg_mixed_persistent(PersistArgs a) {
+  // barrier test: bar[3] != 0 withholds the last block, so the others'
+  // first barrier wait runs out (DEC_ERR_TIMEOUT)
+  if (*(volatile unsigned*)(a.bar + 3) && blockIdx.x == gridDim.x - 1) return;
   const int64_t n = a.n;
   const int64_t gtid = blockIdx.x * (int64_t)kPBlock + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * kPBlock;
@@ -381,6 +389,7 @@ dec_status solve_mixed_persistent(dec_ctx* ctx, int inst, double rtol, int max_i
   int* status = reinterpret_cast<int*>(ctx->coop.p + 2);
   double* result = reinterpret_cast<double*>(ctx->coop.p + 8);
   DEC_TRY(cudaMemsetAsync(ctx->coop.p, 0, 16 * sizeof(int64_t), s));
+  DEC_TRY(write_barrier_test(ctx, bar));
   PersistArgs a{};
   a.n = n;
   a.A32 = sell_arg(ctx->sellL, ctx->sL32.p + (int64_t)vs * ctx->sellL.total);

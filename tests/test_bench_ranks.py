@@ -55,7 +55,7 @@ def test_reference_arm_prints_on_rank_zero_only(rank, prints, tmp_path):
                DEC_INPUT_CACHE=str(tmp_path))
     args = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
             "--workload", "kuhn9", "--steps", "1", "--warmup", "0",
-            "--ref-tets", "500", "--ref-iters", "5"]
+            "--ref-N", "5"]
     r = subprocess.run(args, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
