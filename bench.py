@@ -67,6 +67,28 @@ def max_over_ranks(x, world, device="cpu"):
     return float(t.item())
 
 
+def rank_instances(B, rank, world):
+    """Global ids of the instances rank `rank` solves when each of `world`
+    ranks solves B of them (weak scaling: the work per GPU is fixed, the job
+    solves B * world instances; instances are independent, so the ranks
+    exchange nothing but the k_eff results)."""
+    return list(range(rank * B, (rank + 1) * B))
+
+
+def gather_instances(values, world, device="cpu"):
+    """Every rank's per-instance values, concatenated in global instance
+    order (rank 0's first), on every rank."""
+    v = np.asarray(values, dtype=np.float64)
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(v, dtype=torch.float64, device=device)
+    parts = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(parts, t)
+    return np.concatenate([p.cpu().numpy() for p in parts])
+
+
 def _log(msg):
     print(f"[bench] {msg}", file=sys.stderr, flush=True)
 
@@ -165,6 +187,12 @@ def gpu_arm(args, rank, world):
     _build.build()
     t0 = time.time()
     wl = make_workload(args.workload, N=args.N)
+    B_rank = wl.batch
+    if world > 1 and wl.scales is None and wl.T0.shape[0] > 1:
+        # Dirichlet value sets: rank r solves sets r*B .. r*B + B - 1 of one
+        # recipe drawn for all ranks (set 0, the paper's problem, on rank 0)
+        allw = make_workload(args.workload, N=args.N, n_sets=B_rank * world)
+        wl.T0 = np.ascontiguousarray(allw.T0[rank_instances(B_rank, rank, world)])
     _log(f"inputs {wl.name}: n={wl.n} m={wl.m} in {time.time() - t0:.1f} s")
     stream = torch.cuda.Stream(device=dev)
     ctx = abi.Context(device=dev_id, stream=stream.cuda_stream)
@@ -350,6 +378,8 @@ def gpu_arm(args, rank, world):
         except Exception:
             traffic = None
     clocks = clk.summary()
+    # k_eff of every rank's instances, in global order
+    q_all = gather_instances(q_in, world, dev)
 
     out = {
         "metric": METRIC, "value": round(ms, 4), "unit": "ms",
@@ -359,7 +389,8 @@ def gpu_arm(args, rank, world):
         "dtype": "f64" if want == "fp64" else "f32 (bf16 FSAI values; f64 residual and k_eff)",
         "data": "synthetic, seeded: " + DATA.get(wl.name.split("@")[0], "jittered-lattice Delaunay cube"),
         "config": {"workload": wl.name, "n_nodes": n, "n_tets": m,
-                   "n_edges": ne, "nnz": nnz, "instances": B,
+                   "n_edges": ne, "nnz": nnz, "instances": B * world,
+                   "instances_per_gpu": B,
                    "precond": wl.precond,
                    "mode": want,
                    "rtol": rtol, "l2": "flushed (512 MiB write) between steps",
@@ -367,7 +398,7 @@ def gpu_arm(args, rank, world):
         "iters": int(iters[0]), "relres": float(np.max(relres)),
         "k_eff": float(q_in[0]),
         "iters_per_instance": [int(v) for v in iters] if len(iters) > 1 else None,
-        "k_eff_per_instance": [float(v) for v in q_in] if len(q_in) > 1 else None,
+        "k_eff_per_instance": [float(v) for v in q_all] if len(q_all) > 1 else None,
         "solve_ms": round(solve_ms, 4),
         "phases_ms": phases,
         "other_mode": {"mode": "mixed" if other == abi.DEC_MODE_MIXED else "fp64 per instance",
@@ -402,33 +433,108 @@ def gpu_arm(args, rank, world):
 KERNEL_REV = "r2"
 
 
-def crack_growth_measure(max_steps=600, oracle_steps=3):
-    """Crack growth (max-flux rule) on a mesh of the size of the paper's
-    crack study (a 15^3 jittered Delaunay cube, 3,375 nodes, k = 1): GPU
-    time per step (crack + rebuild + solve + k_eff) over up to max_steps
-    steps, and the oracle's time per step over a few steps on the host."""
+def crack_growth_measure(max_steps=600, oracle_steps=3, paths=64, path_steps=200):
+    """Crack growth on a mesh of the size of the paper's crack study (a 15^3
+    jittered Delaunay cube, 3,375 nodes, k = 1):
+      * max-flux rule (Sec. 3.3): GPU time per step (crack + update + solve +
+        k_eff) with row updates and warm starts, and with a full rebuild and
+        a cold start per step, over up to max_steps steps; CG iterations;
+      * Monte-Carlo paths (Sec. 3.4): `paths` random orders cracked together
+        as one batch, time per path-step over `path_steps` steps;
+      * the oracle's time per step over a few steps on the host."""
     import oracle as O
     from dec_inputs import make_workload
     from paper_2104_05999_gb300 import abi
     wl = make_workload("lognormal64", N=15)
-    ctx = abi.Context(device=int(os.environ.get("LOCAL_RANK", 0)))
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    out = {"mesh": f"15^3 jittered Delaunay cube, k = 1 ({wl.n} nodes, {wl.m} tets)",
+           "rule": "max_flux"}
+    for rebuild in (False, True):
+        ctx = abi.Context(device=dev)
+        ctx.dec_mesh_upload(wl.xyz, wl.tets, wl.tags)
+        ctx.dec_hodge_assemble(None)
+        ctx.dec_laplacian_build(wl.T0[:1], abi.DEC_PRECOND_FSAI)
+        rule = abi.DEC_CRACK_MAX_FLUX | (abi.DEC_CRACK_REBUILD if rebuild else 0)
+        t0 = time.perf_counter()
+        _, cracked, keff = ctx.dec_crack_evolve(rule, max_steps, rtol=1e-10)
+        dt = time.perf_counter() - t0
+        its = ctx.dec_get_crack_iterations()
+        ctx.close()
+        key = "rebuild_cold_start" if rebuild else "row_update_warm_start"
+        out[key] = {"steps": int(len(cracked)),
+                    "ms_per_step": round(1000 * dt / max(1, len(cracked)), 3),
+                    "cg_iters_per_step": round(its / max(1, len(cracked)), 1),
+                    "k_eff_after_first": float(keff[0]), "k_eff_last": float(keff[-1])}
+    out["ms_per_step"] = out["row_update_warm_start"]["ms_per_step"]
+    # Monte-Carlo paths, batched
+    E, t2e = O.edge_list(wl.tets)
+    w = O.hodge_star1(wl.xyz, wl.tets, E, t2e, None)
+    cand = np.flatnonzero(O.crackable_edges(w))
+    orders = np.stack([np.random.default_rng(500 + b).permutation(cand)[:path_steps]
+                       for b in range(paths)]).astype(np.int32)
+    ctx = abi.Context(device=dev)
     ctx.dec_mesh_upload(wl.xyz, wl.tets, wl.tags)
     ctx.dec_hodge_assemble(None)
     ctx.dec_laplacian_build(wl.T0[:1], abi.DEC_PRECOND_FSAI)
     t0 = time.perf_counter()
-    _, cracked, keff = ctx.dec_crack_evolve(abi.DEC_CRACK_MAX_FLUX, max_steps, rtol=1e-10)
+    _, keffs, steps = ctx.dec_crack_paths(orders, rtol=1e-10)
     dt = time.perf_counter() - t0
+    its = ctx.dec_get_crack_iterations()
     ctx.close()
+    done = int(np.sum(steps))
+    out["monte_carlo_paths"] = {
+        "paths": paths, "steps_per_path": path_steps,
+        "ms_per_path_step": round(1000 * dt / max(1, done), 4),
+        "ms_per_batched_step": round(1000 * dt / max(1, int(np.max(steps))), 3),
+        "cg_iters_per_path_step": round(its / max(1, done), 1),
+        "k_eff_last_mean": float(np.mean([k[-1] for k in keffs]))}
     t0 = time.perf_counter()
     O.crack_evolution(wl.xyz, wl.tets, wl.tags, wl.T0[0], k=None,
                       max_steps=oracle_steps, rtol=1e-10)
     ot = (time.perf_counter() - t0) / (oracle_steps + 1)   # + the first solve
-    return {"mesh": f"15^3 jittered Delaunay cube, k = 1 ({wl.n} nodes, {wl.m} tets)",
-            "rule": "max_flux", "steps": int(len(cracked)),
-            "ms_per_step": round(1000 * dt / max(1, len(cracked)), 3),
-            "k_eff_after_first": float(keff[0]), "k_eff_last": float(keff[-1]),
-            "oracle_ms_per_step": round(1000 * ot, 1),
-            "oracle": "oracle.crack_evolution, numpy/scipy FP64, 1 thread"}
+    out["oracle_ms_per_step"] = round(1000 * ot, 1)
+    out["oracle"] = "oracle.crack_evolution, numpy/scipy FP64, 1 thread"
+    return out
+
+
+def fields_measure(n_fields=16, N=64):
+    """Many conductivity fields on one mesh (Sec. 1, Sec. 2.1): `n_fields`
+    lognormal fields (sigma 1) on the 64^3 jittered Delaunay cube, solved as
+    one batch (mixed precision) and one field at a time in FP64; step = Hodge
+    star of every field + L + preconditioners + solve + k_eff."""
+    import torch
+    from dec_inputs import make_fields, make_workload
+    from paper_2104_05999_gb300 import abi
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    wl = make_workload("lognormal64", N=N)
+    k = make_fields(wl, n_fields, sigma=1.0)
+    d = torch.device("cuda", dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(d)  # noqa: E731
+    xyz, tets, tags, T0, kk = t(wl.xyz), t(wl.tets), t(wl.tags), t(wl.T0), t(k)
+    res = {}
+    for name, pc, mode in (("batched", abi.DEC_PRECOND_FSAI_SHARED, abi.DEC_MODE_MIXED_BATCHED),
+                           ("fp64_per_field", abi.DEC_PRECOND_FSAI, abi.DEC_MODE_FP64)):
+        ctx = abi.Context(device=dev)
+        ctx.dec_mesh_upload(xyz, tets, tags)
+        times = []
+        for rep in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.dec_hodge_assemble_fields(kk)
+            ctx.dec_laplacian_build(T0, pc)
+            _, iters, _ = ctx.dec_solve(1e-10, MAX_ITER, mode)
+            q, _, _ = ctx.dec_k_eff()
+            times.append(1000 * (time.perf_counter() - t0))
+        ctx.close()
+        res[name] = (min(times[1:]), q, iters)
+    qb, q64 = res["batched"][1], res["fp64_per_field"][1]
+    return {"mesh": f"64^3 jittered Delaunay cube ({wl.n} nodes, {wl.m} tets)",
+            "fields": n_fields,
+            "batched_ms": round(res["batched"][0], 2),
+            "fp64_per_field_ms": round(res["fp64_per_field"][0], 2),
+            "iters_batched_max": int(np.max(res["batched"][2])),
+            "iters_fp64_max": int(np.max(res["fp64_per_field"][2])),
+            "k_eff_max_rel_diff": float(np.max(np.abs(qb - q64) / np.abs(q64)))}
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -619,6 +725,7 @@ def main():
                                    "cores": 1, "kind": "oracle",
                                    "sample": desc, **detail}
             out["crack_growth"] = crack_growth_measure()
+            out["conductivity_fields"] = fields_measure()
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

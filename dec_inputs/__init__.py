@@ -14,12 +14,14 @@ TetGen meshes.
 from .mesh import (kuhn_lattice, jittered_lattice, delaunay_lattice,
                    canonical_tets, lattice_spacing)
 from .fields import (node_tags, dirichlet_values, lognormal_conductivity,
-                     penny_discs, crack_scales, FREE, DIRICHLET, NEUMANN)
-from .workloads import Workload, make_workload, WORKLOADS
+                     conductivity_fields, penny_discs, crack_scales, FREE,
+                     DIRICHLET, NEUMANN)
+from .workloads import Workload, make_workload, make_fields, WORKLOADS
 
 __all__ = [
     "kuhn_lattice", "jittered_lattice", "delaunay_lattice", "canonical_tets",
     "lattice_spacing", "node_tags", "dirichlet_values",
-    "lognormal_conductivity", "penny_discs", "crack_scales", "FREE",
-    "DIRICHLET", "NEUMANN", "Workload", "make_workload", "WORKLOADS",
+    "lognormal_conductivity", "conductivity_fields", "penny_discs",
+    "crack_scales", "FREE", "DIRICHLET", "NEUMANN", "Workload",
+    "make_workload", "make_fields", "WORKLOADS",
 ]

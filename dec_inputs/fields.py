@@ -44,6 +44,13 @@ def lognormal_conductivity(m: int, sigma: float,
     return np.exp(sigma * rng.standard_normal(m))
 
 
+def conductivity_fields(m: int, n_fields: int, sigma: float,
+                        rng: np.random.Generator) -> np.ndarray:
+    """``n_fields`` independent per-tet lognormal fields, ``f64[n_fields, m]``
+    (field f, tet t: exp(sigma * N(0, 1)))."""
+    return np.exp(sigma * rng.standard_normal((n_fields, m)))
+
+
 def penny_discs(nd: int, rmin: float, rmax: float,
                 rng: np.random.Generator) -> np.ndarray:
     """nd discs: centre U[0,1]^3, normal uniform on the sphere (normalised

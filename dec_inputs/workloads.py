@@ -26,8 +26,8 @@ import os
 
 import numpy as np
 
-from .fields import (crack_scales, dirichlet_values, lognormal_conductivity,
-                     node_tags, penny_discs)
+from .fields import (conductivity_fields, crack_scales, dirichlet_values,
+                     lognormal_conductivity, node_tags, penny_discs)
 from .mesh import delaunay_lattice, jittered_lattice, kuhn_lattice
 
 
@@ -131,3 +131,12 @@ def make_workload(name: str, N: int | None = None, n_discs: int | None = None,
     return Workload(name=name if N == N0 else f"{name}@{N}", N=N, xyz=xyz,
                     tets=tets, tags=tags, T0=T0, k=k, discs=discs,
                     scales=scales, rtol=rtol, precond=precond, mode=mode)
+
+
+def make_fields(wl: Workload, n_fields: int, sigma: float = 1.0) -> np.ndarray:
+    """``n_fields`` lognormal conductivity fields on the mesh of ``wl``
+    (many material fields on one mesh), drawn from their own child stream of
+    the workload's seed, so the workload's other inputs are unchanged."""
+    idx = WORKLOADS[wl.name.split("@")[0]][0]
+    rng = np.random.default_rng(np.random.SeedSequence(1000 + idx).spawn(5)[4])
+    return conductivity_fields(wl.m, n_fields, sigma, rng)

@@ -73,9 +73,10 @@ enum {
   DEC_PRECOND_FSAI_SHARED = 2   /* prepares the batched solve
                                    (DEC_MODE_MIXED_BATCHED): Dirichlet sets
                                    share the FSAI factor of their common L;
-                                   crack states get one FP32-built BF16
-                                   factor each (rows longer than 12 keep the
-                                   uncracked operator's factor)               */
+                                   crack states and conductivity fields get
+                                   one FP32-built BF16 factor each (rows
+                                   longer than 12 keep the factor of the
+                                   uncracked operator, resp. of field 0)      */
 };
 /* solve modes (dec_solve) */
 enum {
@@ -150,6 +151,23 @@ dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k,
                               const double* discs, int64_t n_discs,
                               const double* scales, int32_t n_scales);
 
+/* Several conductivity fields on one mesh (Sec. 1: the same mesh serves
+ * many material fields; Sec. 2.1: conductivity lives on the dual 2-cells):
+ * assemble one Hodge star *1 per field, each as dec_hodge_assemble does for
+ * that field (bit for bit), with one common set of cracks.  The fields then
+ * are the instances of dec_laplacian_build (n_sets must be 1), dec_solve
+ * (every mode; DEC_MODE_MIXED_BATCHED solves all fields in one launch, with
+ * one FSAI factor per field) and dec_k_eff.
+ *   k         [n_fields*n_tets] f64 host or device: field f's conductivity of
+ *             tet t at k[f*n_tets + t]; finite and > 0.
+ *   n_fields  1..64.
+ *   discs, n_discs   as for dec_hodge_assemble (one crack state).
+ * dec_get_hodge reports field 0.  dec_crack_evolve needs a single field.
+ * Errors: DEC_ERR_STATE without a mesh, DEC_ERR_ARG for bad k or discs,
+ * DEC_ERR_LIMIT for more than 64 fields. */
+dec_status dec_hodge_assemble_fields(dec_ctx* ctx, const double* k, int32_t n_fields,
+                                     const double* discs, int64_t n_discs);
+
 /* Build the node Laplacian and the right-hand sides (Sec. 2.3, Eq. 11-13),
  * node form: L_ij = -*1_ij, L_ii = sum_j *1_ij; Dirichlet columns move to
  * the right-hand side (b_i = sum_{j in D} *1_ij T0_j), Dirichlet rows
@@ -159,8 +177,9 @@ dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k,
  *   T0       [n_sets*n_nodes] f64 host or device: Dirichlet values (only
  *            entries at Dirichlet nodes are read).
  *   n_sets   number of Dirichlet value sets (right-hand sides), >= 1.
- *            With n_scales > 1 in dec_hodge_assemble, n_sets must be 1: the
- *            instances are then the crack states.
+ *            With n_scales > 1 in dec_hodge_assemble, or several fields in
+ *            dec_hodge_assemble_fields, n_sets must be 1: the instances are
+ *            then the crack states or the fields.
  *   precond  DEC_PRECOND_JACOBI or DEC_PRECOND_FSAI (factored sparse
  *            approximate inverse on the pattern of lower(L): G^T G ~ L^-1).
  * Errors: DEC_ERR_STATE, DEC_ERR_ARG, DEC_ERR_LIMIT when an FSAI row has
@@ -195,10 +214,10 @@ dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy);
 /* Launch shape the last DEC_MODE_MIXED_BATCHED solve of this context used,
  * as picked by its autotuner: the first batched solve of a problem size
  * (nodes, matrix entries) at each instance stride (8, 16, 32, 64) times a
- * few iterations of every gather variant and keeps the fastest for the
- * context's later solves of that size.
- *   gather_entries  host: 0 = gathers into registers, 4 at a time; G > 0 =
- *                   gathers into shared memory, G entries per round trip.
+ * few iterations of every variant and keeps the fastest for the context's
+ * later solves of that size.
+ *   gather_entries  host: matrix entries whose neighbour rows a thread
+ *                   gathers per round trip (2, 4 or 8).
  * All variants give bit-identical results.  DEC_ERR_STATE before the first
  * batched solve.  (No counterpart in the paper: a launch-shape choice.) */
 dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries);
@@ -213,7 +232,11 @@ dec_status dec_get_batch_kernel_ms(dec_ctx* ctx, double* ms);
 /* crack rules (dec_crack_evolve) */
 enum {
   DEC_CRACK_MAX_FLUX = 0,   /* the face with the largest flux cracks (Sec. 3.3)   */
-  DEC_CRACK_ORDER = 1       /* faces crack in a caller-drawn order (Sec. 3.4)     */
+  DEC_CRACK_ORDER = 1,      /* faces crack in a caller-drawn order (Sec. 3.4)     */
+  DEC_CRACK_REBUILD = 16    /* or-ed into a rule: rebuild L, b and the
+                               preconditioner and solve from zero at every
+                               step, instead of updating the changed rows and
+                               starting from the previous solution            */
 };
 
 /* Crack growth (Sec. 2.5; deterministic cracking Sec. 3.3, stochastic
@@ -221,8 +244,13 @@ enum {
  * dec_laplacian_build with one Dirichlet set, no crack states and
  * DEC_PRECOND_JACOBI or DEC_PRECOND_FSAI), solve, then repeat: crack one
  * dual face (its edge's *1 becomes 0 for L, b, the preconditioner and
- * k_eff), rebuild L and the preconditioner, solve again from zero, record
- * k_eff.  Candidates are the edges that still conduct (*1 > 0, not cut):
+ * k_eff), solve again, record k_eff.  A crack changes a few values of the
+ * system only (Sec. 2.3): each step recomputes rows i and j of L and b (as a
+ * full build would), the FSAI rows whose lower-pattern block holds i or j
+ * (or the two Jacobi entries), and starts PCG from the previous solution;
+ * with DEC_CRACK_REBUILD or-ed into the rule it rebuilds L and the
+ * preconditioner and solves from zero instead.  The stopping rule is the
+ * same either way: ||b - L u|| <= rtol ||b||.  Candidates are the edges that still conduct (*1 > 0, not cut):
  * in the node form every dual face lies between two dual cells.
  *   rule      DEC_CRACK_MAX_FLUX: the candidate with the largest
  *             |*1_e (T_i - T_j)| in the current solution (the flux 2-form on
@@ -246,6 +274,36 @@ enum {
 dec_status dec_crack_evolve(dec_ctx* ctx, int32_t rule, int32_t max_steps,
                             const int32_t* order, double rtol, int32_t max_iter, int32_t mode,
                             double k_stop, int32_t* cracked, double* k_eff, int32_t* steps);
+
+/* Stochastic cracking of several Monte-Carlo paths at once (Sec. 3.4: the
+ * damage at which the domain stops conducting, over many random orders).
+ * Starting from the current state (as for dec_crack_evolve: one Dirichlet
+ * set, no crack states, one conductivity field), path b cracks the edges
+ * orders[b][0], orders[b][1], ... one per step, each in its own copy of *1;
+ * after every step all paths are solved together by the batched mixed
+ * solve (one instance per path, one FSAI factor per path, every solve
+ * started from the previous solutions) and k_eff is recorded.  A path stops
+ * after the step whose k_eff <= k_stop * its uncracked k_eff.
+ *   n_paths   2..64.
+ *   orders    [n_paths*max_steps] int32 edge ids, host or device.
+ *   rtol, max_iter   as for dec_solve.
+ *   k_eff     [n_paths*max_steps] f64 host: q_in of path b after step s at
+ *             k_eff[b*max_steps + s] (entries past a path's last step are
+ *             not written).
+ *   steps     [n_paths] int32 host: steps done per path.
+ * Afterwards the context holds the paths as instances (dec_k_eff reports
+ * each path's last state; dec_solve with DEC_MODE_MIXED_BATCHED solves them
+ * again).  Errors: DEC_ERR_STATE, DEC_ERR_ARG (also for an order entry that
+ * is not a conducting, uncut edge of its path; the steps before it are
+ * kept), and the errors of dec_solve. */
+dec_status dec_crack_paths(dec_ctx* ctx, int32_t n_paths, int32_t max_steps,
+                           const int32_t* orders, double rtol, int32_t max_iter,
+                           double k_stop, double* k_eff, int32_t* steps);
+
+/* CG iterations summed over the steps of the last dec_crack_evolve or
+ * dec_crack_paths call (over all paths; the first solve before any crack
+ * not counted). */
+dec_status dec_get_crack_iterations(const dec_ctx* ctx, int64_t* iters);
 
 /* ---- sizes and intermediate results (parity checks, debugging) ---- */
 

@@ -35,7 +35,7 @@ DEC_PRECOND_JACOBI, DEC_PRECOND_FSAI, DEC_PRECOND_FSAI_SHARED = 0, 1, 2
 DEC_MODE_FP64, DEC_MODE_MIXED, DEC_MODE_MIXED_PHASED, DEC_MODE_MIXED_BATCHED = 0, 1, 2, 3
 DEC_KERNEL_SPMV_F64, DEC_KERNEL_SPMV_F32 = 0, 1
 DEC_KERNEL_FSAI_F64, DEC_KERNEL_FSAI_BF16 = 2, 3
-DEC_CRACK_MAX_FLUX, DEC_CRACK_ORDER = 0, 1
+DEC_CRACK_MAX_FLUX, DEC_CRACK_ORDER, DEC_CRACK_REBUILD = 0, 1, 16
 
 _P = C.c_void_p
 _I64 = C.c_int64
@@ -48,12 +48,15 @@ SIGNATURES = {
     "dec_destroy": [_P],
     "dec_mesh_upload": [_P, _P, _I64, _P, _I64, _P],
     "dec_hodge_assemble": [_P, _P, _P, _I64, _P, _I32],
+    "dec_hodge_assemble_fields": [_P, _P, _I32, _P, _I64],
     "dec_laplacian_build": [_P, _P, _I32, _I32],
     "dec_solve": [_P, _D, _I32, _I32, _P, _P, _P],
     "dec_k_eff": [_P, _P, _P, _P],
     "dec_crack_evolve": [_P, _I32, _I32, _P, _D, _I32, _I32, _D, _P, _P, _P],
     "dec_get_batch_variant": [_P, _P],
     "dec_get_batch_kernel_ms": [_P, _P],
+    "dec_get_crack_iterations": [_P, _P],
+    "dec_crack_paths": [_P, _I32, _I32, _P, _D, _I32, _D, _P, _P],
     "dec_get_sizes": [_P, _P, _P, _P, _P, _P],
     "dec_get_edges": [_P, _P, _P],
     "dec_get_hodge": [_P, _P, _P],
@@ -161,6 +164,12 @@ class Context:
             self.h, _ptr(k, np.float64), _ptr(discs, np.float64), nd,
             _ptr(scales, np.float64), ns))
 
+    def dec_hodge_assemble_fields(self, k, discs=None):
+        """k: [n_fields, n_tets] conductivity fields (one *1 per field)."""
+        nd = 0 if discs is None else len(discs)
+        return self._check(self.lib.dec_hodge_assemble_fields(
+            self.h, _ptr(k, np.float64), int(k.shape[0]), _ptr(discs, np.float64), nd))
+
     def dec_laplacian_build(self, T0, precond=DEC_PRECOND_FSAI):
         n_sets = 1 if T0.ndim == 1 else T0.shape[0]
         return self._check(self.lib.dec_laplacian_build(
@@ -210,12 +219,34 @@ class Context:
         k = steps.value
         return st, cracked[:k].copy(), keff[:k].copy()
 
+    def dec_crack_paths(self, orders, rtol=1e-10, max_iter=100000, k_stop=1e-9,
+                        raise_on_error=True):
+        """Stochastic cracking of several paths at once; ``orders`` is
+        [n_paths, max_steps].  Returns (status, k_eff per path trimmed to
+        its steps, steps per path)."""
+        orders = np.ascontiguousarray(orders, dtype=np.int32)
+        P, S = orders.shape
+        keff = np.zeros((P, max(S, 1)))
+        steps = np.zeros(P, dtype=np.int32)
+        st = self.lib.dec_crack_paths(self.h, int(P), int(S), orders.ctypes.data,
+                                      float(rtol), int(max_iter), float(k_stop),
+                                      keff.ctypes.data, steps.ctypes.data)
+        if raise_on_error:
+            self._check(st)
+        return st, [keff[b, :steps[b]].copy() for b in range(P)], steps
+
     # ---- getters --------------------------------------------------------
     def dec_get_batch_variant(self):
         """Gather entries per round trip the autotuner picked for the last
         batched solve (0: register gathers)."""
         v = C.c_int32()
         self._check(self.lib.dec_get_batch_variant(self.h, C.byref(v)))
+        return v.value
+
+    def dec_get_crack_iterations(self):
+        """CG iterations summed over the steps of the last crack growth."""
+        v = C.c_int64()
+        self._check(self.lib.dec_get_crack_iterations(self.h, C.byref(v)))
         return v.value
 
     def dec_get_batch_kernel_ms(self):

@@ -145,12 +145,14 @@ dec_status dec_mesh_upload(dec_ctx* ctx, const double* xyz, int64_t n_nodes,
   return DEC_OK;
 }
 
-dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k, const double* discs,
-                              int64_t n_discs, const double* scales,
-                              int32_t n_scales) {
-  if (!ctx) return DEC_ERR_ARG;
-  ctx->err.clear();
-  if (ctx->stage < 1) return ctx->fail(DEC_ERR_STATE, "hodge_assemble: no mesh uploaded");
+}  // extern "C"
+
+namespace {
+
+// Shared part of dec_hodge_assemble and dec_hodge_assemble_fields: k holds
+// n_fields conductivity fields of n_tets values each (or NULL).
+dec_status hodge_common(dec_ctx* ctx, const double* k, int n_fields, const double* discs,
+                        int64_t n_discs, const double* scales, int32_t n_scales) {
   if (n_discs < 0 || (n_discs > 0 && !discs))
     return ctx->fail(DEC_ERR_ARG, "hodge_assemble: bad discs / n_discs");
   if (n_discs >= INT32_MAX) return ctx->fail(DEC_ERR_LIMIT, "hodge_assemble: too many discs");
@@ -162,8 +164,8 @@ dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k, const double* discs
   // conductivity: finite and > 0
   const bool has_k = k != nullptr;
   if (has_k) {
-    DEC_TRY(upload(ctx->kcond, k, ctx->m, s));
-    DEC_TRY_STATUS(dec::validate_k(ctx));
+    DEC_TRY(upload(ctx->kcond, k, (int64_t)n_fields * ctx->m, s));
+    DEC_TRY_STATUS(dec::validate_k(ctx, (int64_t)n_fields * ctx->m));
   }
   std::vector<double> hs;
   if (scales) {
@@ -175,6 +177,7 @@ dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k, const double* discs
     hs.assign(1, 1.0);
   }
   ctx->n_scales = (int)hs.size();
+  ctx->n_fields = n_fields;
   DEC_TRY(upload(ctx->scales, hs.data(), (int64_t)hs.size(), s));
   if (n_discs > 0) {
     std::vector<double> hd;
@@ -189,10 +192,34 @@ dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k, const double* discs
     }
     DEC_TRY(upload(ctx->discs, hd.data(), 7 * n_discs, s));
   }
-  DEC_TRY_STATUS(dec::assemble_hodge(ctx, n_discs, has_k));
+  DEC_TRY_STATUS(dec::assemble_hodge(ctx, n_discs, has_k, n_fields));
   DEC_TRY(cudaStreamSynchronize(s));
   ctx->stage = 2;
   return DEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k, const double* discs,
+                              int64_t n_discs, const double* scales,
+                              int32_t n_scales) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 1) return ctx->fail(DEC_ERR_STATE, "hodge_assemble: no mesh uploaded");
+  return hodge_common(ctx, k, 1, discs, n_discs, scales, n_scales);
+}
+
+dec_status dec_hodge_assemble_fields(dec_ctx* ctx, const double* k, int32_t n_fields,
+                                     const double* discs, int64_t n_discs) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 1) return ctx->fail(DEC_ERR_STATE, "hodge_assemble_fields: no mesh uploaded");
+  if (!k || n_fields < 1) return ctx->fail(DEC_ERR_ARG, "hodge_assemble_fields: bad k / n_fields");
+  if (n_fields > 64)
+    return ctx->fail(DEC_ERR_LIMIT, "hodge_assemble_fields: at most 64 conductivity fields");
+  return hodge_common(ctx, k, n_fields, discs, n_discs, nullptr, 0);
 }
 
 dec_status dec_laplacian_build(dec_ctx* ctx, const double* T0, int32_t n_sets,
@@ -204,19 +231,20 @@ dec_status dec_laplacian_build(dec_ctx* ctx, const double* T0, int32_t n_sets,
   if (precond != DEC_PRECOND_JACOBI && precond != DEC_PRECOND_FSAI &&
       precond != DEC_PRECOND_FSAI_SHARED)
     return ctx->fail(DEC_ERR_ARG, "laplacian_build: unknown preconditioner");
-  if (ctx->n_scales > 1 && n_sets > 1)
-    return ctx->fail(DEC_ERR_ARG, "laplacian_build: crack states and several T0 sets at once");
+  if ((ctx->n_scales > 1 || ctx->n_fields > 1) && n_sets > 1)
+    return ctx->fail(DEC_ERR_ARG,
+                     "laplacian_build: crack states or fields and several T0 sets at once");
   DEC_TRY_STATUS(set_device(ctx));
   cudaStream_t s = ctx->stream;
   ctx->stage = 2;
   const int64_t n = ctx->n, nnz = ctx->nnz;
   ctx->n_sets = n_sets;
   ctx->precond = precond;
-  ctx->B = std::max(ctx->n_scales, n_sets);
+  ctx->B = std::max(std::max(ctx->n_scales, ctx->n_fields), n_sets);
   const bool shared = precond == DEC_PRECOND_FSAI_SHARED;
   if (shared && ctx->B > 64)
     return ctx->fail(DEC_ERR_LIMIT, "laplacian_build: a batched solve takes at most 64 instances");
-  const int V = shared ? 1 : ctx->n_scales;  // value sets
+  const int V = shared ? 1 : std::max(ctx->n_scales, ctx->n_fields);  // value sets
   DEC_TRY(upload(ctx->T0, T0, (int64_t)n_sets * n, s));
   DEC_TRY(ctx->val64.ensure((size_t)V * nnz));
   DEC_TRY(ctx->sL64.ensure((size_t)V * ctx->sellL.total));
@@ -267,7 +295,7 @@ dec_status dec_solve(dec_ctx* ctx, double rtol, int32_t max_iter, int32_t mode,
   const int64_t n = ctx->n;
   ctx->stage = 3;
   DEC_TRY(ctx->u.ensure((size_t)ctx->B * n));
-  DEC_TRY(ctx->out3.ensure(3 * (size_t)ctx->B + 1));
+  DEC_TRY(ctx->out3.ensure(3 * (size_t)ctx->B + 2));
   if (mode == DEC_MODE_FP64) {
     for (auto* bf : {&ctx->x64, &ctx->r64, &ctx->z64, &ctx->p64, &ctx->q64, &ctx->t64})
       DEC_TRY(bf->ensure(n));
@@ -316,11 +344,13 @@ dec_status dec_crack_evolve(dec_ctx* ctx, int32_t rule, int32_t max_steps,
     return ctx->fail(DEC_ERR_STATE,
                      "crack_evolve: needs one instance (one Dirichlet set, no crack states) "
                      "and a per-instance preconditioner");
-  if (rule != DEC_CRACK_MAX_FLUX && rule != DEC_CRACK_ORDER)
+  const int base_rule = rule & ~DEC_CRACK_REBUILD;
+  if (base_rule != DEC_CRACK_MAX_FLUX && base_rule != DEC_CRACK_ORDER)
     return ctx->fail(DEC_ERR_ARG, "crack_evolve: unknown rule");
   if (mode != DEC_MODE_FP64 && mode != DEC_MODE_MIXED && mode != DEC_MODE_MIXED_PHASED)
     return ctx->fail(DEC_ERR_ARG, "crack_evolve: mode must be FP64, MIXED or MIXED_PHASED");
-  if (max_steps < 0 || !cracked || !k_eff || !steps || (rule == DEC_CRACK_ORDER && !order && max_steps > 0))
+  if (max_steps < 0 || !cracked || !k_eff || !steps ||
+      (base_rule == DEC_CRACK_ORDER && !order && max_steps > 0))
     return ctx->fail(DEC_ERR_ARG, "crack_evolve: bad max_steps or NULL output / order");
   if (!(rtol > 0.0) || !std::isfinite(rtol) || max_iter < 1 || !(k_stop >= 0.0))
     return ctx->fail(DEC_ERR_ARG, "crack_evolve: rtol > 0, max_iter >= 1, k_stop >= 0");
@@ -328,9 +358,9 @@ dec_status dec_crack_evolve(dec_ctx* ctx, int32_t rule, int32_t max_steps,
   cudaStream_t s = ctx->stream;
   const int64_t n = ctx->n;
   std::vector<int32_t> ord;
-  if (rule == DEC_CRACK_ORDER) DEC_TRY(host_copy(ord, order, max_steps, s));
+  if (base_rule == DEC_CRACK_ORDER) DEC_TRY(host_copy(ord, order, max_steps, s));
   DEC_TRY(ctx->u.ensure((size_t)n));
-  DEC_TRY(ctx->out3.ensure(4));
+  DEC_TRY(ctx->out3.ensure(5));
   if (mode == DEC_MODE_FP64) {
     for (auto* bf : {&ctx->x64, &ctx->r64, &ctx->z64, &ctx->p64, &ctx->q64, &ctx->t64})
       DEC_TRY(bf->ensure(n));
@@ -413,7 +443,7 @@ dec_status dec_get_csr(dec_ctx* ctx, int32_t inst, int32_t* rowptr, int32_t* col
   cudaStream_t s = ctx->stream;
   DEC_TRY(download(rowptr, (const int32_t*)ctx->rowptr.p, ctx->n + 1, s));
   DEC_TRY(download(col, (const int32_t*)ctx->col.p, ctx->nnz, s));
-  const int vs = (ctx->n_scales > 1 && ctx->precond != DEC_PRECOND_FSAI_SHARED) ? inst : 0;
+  const int vs = ctx->precond != DEC_PRECOND_FSAI_SHARED ? dec::value_set(ctx, inst) : 0;
   if (val) DEC_TRY(download(val, (const double*)ctx->val64.p + (int64_t)vs * ctx->nnz, ctx->nnz, s));
   if (b) DEC_TRY(download(b, (const double*)ctx->b.p + (int64_t)inst * ctx->n, ctx->n, s));
   DEC_TRY(cudaStreamSynchronize(s));
@@ -456,6 +486,41 @@ dec_status dec_time_kernel(dec_ctx* ctx, int32_t kernel, int32_t reps,
     return ctx->fail(DEC_ERR_STATE, "time_kernel: no FSAI factor built");
   DEC_TRY_STATUS(set_device(ctx));
   return dec::time_kernel(ctx, kernel, reps, (size_t)flush_bytes, avg_ms);
+}
+
+dec_status dec_crack_paths(dec_ctx* ctx, int32_t n_paths, int32_t max_steps,
+                           const int32_t* orders, double rtol, int32_t max_iter,
+                           double k_stop, double* k_eff, int32_t* steps) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 3) return ctx->fail(DEC_ERR_STATE, "crack_paths: no Laplacian built");
+  if (ctx->B != 1 || ctx->n_scales != 1 || ctx->n_fields != 1)
+    return ctx->fail(DEC_ERR_STATE,
+                     "crack_paths: needs one instance (one Dirichlet set, no crack states, "
+                     "one conductivity field)");
+  if (n_paths < 2 || n_paths > 64)
+    return ctx->fail(DEC_ERR_ARG, "crack_paths: n_paths must be in [2, 64]");
+  if (max_steps < 0 || (max_steps > 0 && (!orders || !k_eff)) || !steps)
+    return ctx->fail(DEC_ERR_ARG, "crack_paths: bad max_steps or NULL orders / outputs");
+  if (!(rtol > 0.0) || !std::isfinite(rtol) || max_iter < 1 || !(k_stop >= 0.0))
+    return ctx->fail(DEC_ERR_ARG, "crack_paths: rtol > 0, max_iter >= 1, k_stop >= 0");
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  DevBuf<int32_t> ord;
+  if (max_steps > 0) DEC_TRY(upload(ord, orders, (int64_t)n_paths * max_steps, s));
+  ctx->stage = 3;
+  dec_status st = dec::crack_paths(ctx, n_paths, max_steps, ord.p, rtol, max_iter, k_stop,
+                                   k_eff, steps);
+  DEC_TRY(cudaStreamSynchronize(s));
+  ord.release();
+  if (st == DEC_OK) ctx->stage = 4;   // the paths' last solutions are current
+  return st;
+}
+
+dec_status dec_get_crack_iterations(const dec_ctx* ctx, int64_t* iters) {
+  if (!ctx || !iters) return DEC_ERR_ARG;
+  *iters = ctx->crack_iters;
+  return DEC_OK;
 }
 
 dec_status dec_get_batch_kernel_ms(dec_ctx* ctx, double* ms) {

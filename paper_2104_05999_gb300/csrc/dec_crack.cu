@@ -10,10 +10,18 @@
 // between the dual cells of two nodes, the counterpart of the paper's
 // non-boundary faces.  A crack marks the edge as cut in crack state 0, so
 // L, b, the preconditioner and k_eff all see w_e = 0 from then on.
+//
+// A crack changes only a few values of the system (Sec. 2.3): rows and
+// columns i, j of L, b_i, b_j, and the FSAI rows whose principal block holds
+// i or j.  Each step updates just those and starts the solve from the
+// previous solution; DEC_CRACK_REBUILD rebuilds everything and solves from
+// zero instead.
 #include "dec_internal.cuh"
 
 #include <algorithm>
 #include <cstdint>
+#include <string>
+#include <vector>
 
 namespace dec {
 
@@ -115,14 +123,20 @@ dec_status crack_evolve(dec_ctx* ctx, int rule, int max_steps, const int32_t* or
   double* bval = ctx->partial.p;   // capacity >= 8 blocks per SM
   *steps = 0;
   int it = 0;
+  int64_t iters_total = 0;
   double rr = 0.0, o[3];
-  auto solve = [&]() -> dec_status {
-    dec_status st = solve_instance(ctx, 0, rtol, max_iter, mode, &it, &rr);
+  // rule bit DEC_CRACK_REBUILD: rebuild L and the preconditioner and solve
+  // from zero at every step (the reference behaviour); otherwise update the
+  // rows a crack changes and start each solve from the previous solution
+  const bool rebuild = (rule & DEC_CRACK_REBUILD) != 0;
+  rule &= ~DEC_CRACK_REBUILD;
+  auto solve = [&](bool warm) -> dec_status {
+    dec_status st = solve_instance(ctx, 0, rtol, max_iter, mode, &it, &rr, warm);
     if (st != DEC_OK) return st;
     DEC_TRY_STATUS(form_T(ctx, 0, ctx->t64.p));   // T for the next pick
     return k_eff_all(ctx, o);                     // as dec_k_eff reports it
   };
-  DEC_TRY_STATUS(solve());
+  DEC_TRY_STATUS(solve(false));
   const double k0 = o[0];
   for (int step = 0; step < max_steps; ++step) {
     if (rule == DEC_CRACK_MAX_FLUX) {
@@ -142,14 +156,117 @@ dec_status crack_evolve(dec_ctx* ctx, int rule, int max_steps, const int32_t* or
       return ctx->fail(DEC_ERR_ARG, "crack_evolve: order[" + std::to_string(step) +
                                         "] is not a conducting, uncut edge");
     if (e < 0) break;   // nothing conducts any more
-    DEC_TRY_STATUS(build_values(ctx, 0));
-    DEC_TRY_STATUS(build_precond(ctx, 0));
-    DEC_TRY_STATUS(solve());
+    if (rebuild) {
+      DEC_TRY_STATUS(build_values(ctx, 0));
+      DEC_TRY_STATUS(build_precond(ctx, 0));
+    } else {
+      DEC_TRY_STATUS(crack_update(ctx, e));
+    }
+    DEC_TRY_STATUS(solve(!rebuild));
+    iters_total += it;
     cracked[step] = (int32_t)e;
     k_eff[step] = o[0];
     *steps = step + 1;
     if (o[0] <= k_stop * k0) break;
   }
+  ctx->crack_iters = iters_total;
+  return DEC_OK;
+}
+
+// ------------------------------------------------ Monte-Carlo paths
+// Stochastic cracking (Sec. 3.4) of several paths at once: path b cracks
+// the edges of its own caller-drawn order, one per step, in its own copy of
+// *1 (w[b][e] = 0).  The paths are the instances of one batched solve, each
+// step started from the previous solutions.
+
+// Crack edge order[b][step] of every active path; an entry that is not a
+// conducting, uncut edge of its path sets *bad = path + 1.
+__global__ void crack_paths_take_kernel(int P, int step, int max_steps,
+                                        const int32_t* __restrict__ orders,
+                                        const uint8_t* __restrict__ active, int64_t ne,
+                                        double* __restrict__ w, const uint8_t* __restrict__ fc,
+                                        int* __restrict__ bad) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= P || !active[b]) return;
+  const int64_t e = orders[(int64_t)b * max_steps + step];
+  if (e < 0 || e >= ne || !(w[(int64_t)b * ne + e] > 0.0) || fc[e] == 0) {
+    atomicMax(bad, b + 1);
+    return;
+  }
+  w[(int64_t)b * ne + e] = 0.0;
+}
+
+dec_status crack_paths(dec_ctx* ctx, int P, int max_steps, const int32_t* orders_dev,
+                       double rtol, int max_iter, double k_stop, double* k_eff,
+                       int32_t* steps) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n, ne = ctx->ne;
+  // P copies of the current *1 (field 0), one per path
+  DEC_TRY(cudaStreamSynchronize(s));
+  DEC_TRY(ctx->w.grow_keep((size_t)P * ne, ne));
+  for (int b = 1; b < P; ++b)
+    DEC_TRY(cudaMemcpyAsync(ctx->w.p + (int64_t)b * ne, ctx->w.p, sizeof(double) * ne,
+                            cudaMemcpyDeviceToDevice, s));
+  ctx->n_fields = P;
+  ctx->B = P;
+  ctx->precond = DEC_PRECOND_FSAI_SHARED;
+  DEC_TRY(ctx->b.ensure((size_t)P * n));
+  DEC_TRY(ctx->u.ensure((size_t)P * n));
+  DEC_TRY(ctx->out3.ensure(3 * (size_t)P + 2));
+  // the shared FSAI factor (kept by long rows) needs its buffers even when
+  // the context was built with Jacobi
+  DEC_TRY(ctx->g64.ensure(ctx->nnz));
+  DEC_TRY(ctx->sGlo64.ensure(ctx->sellLo.total));
+  DEC_TRY(ctx->sGup64.ensure(ctx->sellUp.total));
+  DEC_TRY(ctx->sGlo16.ensure(ctx->sellLo.total));
+  DEC_TRY(ctx->sGup16.ensure(ctx->sellUp.total));
+  DEC_TRY_STATUS(build_values(ctx, 0));
+  DEC_TRY_STATUS(build_precond(ctx, 0));   // the factor long rows keep
+  DEC_TRY_STATUS(batch_setup(ctx));
+  std::vector<int> it(P);
+  std::vector<double> rr(P), o(3 * (size_t)P), k0(P);
+  std::vector<uint8_t> act(P, 1);
+  dec_status st = solve_batched(ctx, rtol, max_iter, it.data(), rr.data(), false);
+  if (st != DEC_OK) return st;
+  DEC_TRY_STATUS(k_eff_all(ctx, o.data()));
+  for (int b = 0; b < P; ++b) {
+    k0[b] = o[3 * b];
+    steps[b] = 0;
+  }
+  DEC_TRY(ctx->crack_buf.ensure(((size_t)P + 15) / 8 + 2));
+  uint8_t* d_act = reinterpret_cast<uint8_t*>(ctx->crack_buf.p + 1);
+  int* d_bad = reinterpret_cast<int*>(ctx->crack_buf.p);
+  int64_t iters_total = 0;
+  for (int step = 0; step < max_steps; ++step) {
+    int live = 0;
+    for (int b = 0; b < P; ++b) live += act[b];
+    if (!live) break;
+    DEC_TRY(cudaMemcpyAsync(d_act, act.data(), P, cudaMemcpyHostToDevice, s));
+    DEC_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+    crack_paths_take_kernel<<<(P + 63) / 64, 64, 0, s>>>(P, step, max_steps, orders_dev, d_act,
+                                                       ne, ctx->w.p, ctx->first_cut.p, d_bad);
+    DEC_TRY(cudaGetLastError());
+    ctx->launches += 1;
+    int bad = 0;
+    DEC_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DEC_TRY(cudaStreamSynchronize(s));
+    if (bad)
+      return ctx->fail(DEC_ERR_ARG, "crack_paths: orders[" + std::to_string(bad - 1) + "][" +
+                                        std::to_string(step) +
+                                        "] is not a conducting, uncut edge of its path");
+    DEC_TRY_STATUS(batch_refresh_values(ctx));
+    st = solve_batched(ctx, rtol, max_iter, it.data(), rr.data(), true);
+    if (st != DEC_OK) return st;
+    for (int b = 0; b < P; ++b) iters_total += it[b];
+    DEC_TRY_STATUS(k_eff_all(ctx, o.data()));
+    for (int b = 0; b < P; ++b) {
+      if (!act[b]) continue;
+      k_eff[(int64_t)b * max_steps + step] = o[3 * b];
+      steps[b] = step + 1;
+      if (o[3 * b] <= k_stop * k0[b]) act[b] = 0;
+    }
+  }
+  ctx->crack_iters = iters_total;
   return DEC_OK;
 }
 

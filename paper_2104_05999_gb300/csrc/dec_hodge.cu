@@ -290,6 +290,37 @@ __global__ void edge_reduce_kernel(const int32_t* __restrict__ seg_start,
   }
 }
 
+// *1 of conductivity fields 1..F-1 (field 0 comes from edge_reduce_kernel):
+// the same fixed-order sums with k_f[t] u_T in place of k_0[t] u_T, so a
+// field's *1 equals, bit for bit, what a single-field assembly with that k
+// gives.
+__global__ void edge_reduce_fields_kernel(const int32_t* __restrict__ seg_start,
+                                          const uint32_t* __restrict__ seg_pay,
+                                          const double* __restrict__ piece,
+                                          const double* __restrict__ upart,
+                                          const double* __restrict__ kf, int64_t m, int F,
+                                          int64_t ne, double* __restrict__ w) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double sum = 0.0, u = 0.0;
+    const int32_t k0 = seg_start[e], k1 = seg_start[e + 1];
+    for (int32_t k = k0; k < k1; ++k) {
+      const uint32_t p = seg_pay[k];
+      sum += piece[p];
+      u += upart[p];
+    }
+    for (int f = 1; f < F; ++f) {
+      const double* kk = kf + (int64_t)f * m;
+      double ku = 0.0;
+      for (int32_t k = k0; k < k1; ++k) {
+        const uint32_t p = seg_pay[k];
+        ku += __dmul_rn(kk[p / 6], upart[p]);   // the product kpart holds: no FMA
+      }
+      w[(int64_t)f * ne + e] = u > 0.0 ? sum * (ku / u) : 0.0;
+    }
+  }
+}
+
 // uniform grid of disc bounding boxes (radius scaled by the largest state)
 __global__ void disc_bin_kernel(const double* __restrict__ discs, int nd,
                                 double smax, DiscGrid g, int32_t* __restrict__ counts,
@@ -329,12 +360,12 @@ __global__ void validate_k_kernel(const double* __restrict__ k, int64_t m, int* 
 }
 
 // conductivity must be finite and > 0 (checked on the device)
-dec_status validate_k(dec_ctx* ctx) {
+dec_status validate_k(dec_ctx* ctx, int64_t count) {
   cudaStream_t s = ctx->stream;
   DEC_TRY(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
   const unsigned g = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((ctx->m + 255) / 256, (int64_t)ctx->num_sms * 16));
-  validate_k_kernel<<<g, 256, 0, s>>>(ctx->kcond.p, ctx->m, ctx->errflag.p);
+      1, std::min<int64_t>((count + 255) / 256, (int64_t)ctx->num_sms * 16));
+  validate_k_kernel<<<g, 256, 0, s>>>(ctx->kcond.p, count, ctx->errflag.p);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 1;
   int flag = 0;
@@ -344,12 +375,12 @@ dec_status validate_k(dec_ctx* ctx) {
   return DEC_OK;
 }
 
-dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k) {
+dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k, int n_fields) {
   cudaStream_t s = ctx->stream;
   const int64_t m = ctx->m, q = 6 * m;
   DEC_TRY(ctx->piece.ensure(has_k ? 3 * q : q));   // [piece | k u | u]
   DEC_TRY(ctx->slot_cut.ensure(q));
-  DEC_TRY(ctx->w.ensure(ctx->ne));
+  DEC_TRY(ctx->w.ensure((size_t)n_fields * ctx->ne));
   DEC_TRY(ctx->first_cut.ensure(ctx->ne));
   DiscGrid g{};
   g.nd = (int)nd;
@@ -423,6 +454,13 @@ dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k) {
       ctx->w.p, ctx->first_cut.p);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 2;
+  if (n_fields > 1) {
+    edge_reduce_fields_kernel<<<(unsigned)std::max<int64_t>(eb, 1), 256, 0, s>>>(
+        ctx->seg_start.p, ctx->seg_pay.p, ctx->piece.p, ctx->piece.p + 2 * q, ctx->kcond.p, m,
+        n_fields, ctx->ne, ctx->w.p);
+    DEC_TRY(cudaGetLastError());
+    ctx->launches += 1;
+  }
   return DEC_OK;
 }
 

@@ -31,6 +31,18 @@ struct DevBuf {
     if (e == cudaSuccess) cap = n;
     return e;
   }
+  // like ensure, but a reallocation keeps the first `keep` elements
+  cudaError_t grow_keep(size_t n, size_t keep) {
+    if (n <= cap && p) return cudaSuccess;
+    T* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (p && keep) e = cudaMemcpy(q, p, (keep < cap ? keep : cap) * sizeof(T), cudaMemcpyDeviceToDevice);
+    if (p) cudaFree(p);
+    p = q;
+    cap = n;
+    return e;
+  }
   void release() {
     if (p) cudaFree(p);
     p = nullptr;
@@ -63,6 +75,7 @@ struct SellLayout {
   DevBuf<int32_t> col;    // [total] column of entry j of lane l: sptr[s]+32j+l
   DevBuf<int32_t> pos;    // [nnz] CSR slot -> SELL slot, -1 if absent
   int64_t nslices = 0, total = 0;
+  int C = 32, R = 512;    // rows per slice, rows per window
   void release() { perm.release(); len.release(); sptr.release(); col.release(); pos.release(); }
 };
 
@@ -140,18 +153,34 @@ struct dec_ctx {
   dec::DevBuf<__nv_bfloat16> sGlo16, sGup16;
   dec::DevBuf<int32_t> big_rows;   // FSAI rows for the warp-per-row kernel
   dec::DevBuf<int64_t> coop;       // persistent solve: barrier, status, result
-  // batched solve: shared per-entry data, factor copy, [n][BS] vectors
-  dec::DevBuf<float> bw32;
-  dec::DevBuf<double> bw64, bb, bx64, br64, bpartial;
-  dec::DevBuf<uint8_t> bfc;
+  // batched solve: sliced layouts over spatial windows, per-entry data,
+  // [n][BS] vectors
+  int batch_kind = 0;                      // 0 Dirichlet sets, 1 crack states, 2 fields
+  int batch_BS = 0;                        // instance stride of the layouts
+  dec::DevBuf<int32_t> morton;             // [n] node order of the windows
+  dec::DevBuf<int32_t> mrank;              // [n] position of each node in that order
+  dec::SellLayout bL, bGlo, bGup;          // L (edge or CSR form), G, G^T
+  dec::DevBuf<int2> bLcw;                  // (column, FP32 value bits) per L entry
+  dec::DevBuf<uint8_t> bLfc;               // first crack state per L entry (states)
+  dec::DevBuf<float> bLw;                  // [total][BS] *1 per instance (fields)
+  dec::DevBuf<double> bL64;                // FP64 values, [total] or [total][BS]
+  dec::DevBuf<float> bd32;                 // [n] diagonal (Dirichlet sets)
+  dec::DevBuf<double> bd64;
+  dec::DevBuf<__nv_bfloat16> bGlo16, bGup16;   // shared factor halves
+  dec::DevBuf<__nv_bfloat16> bGloB, bGupB;     // per-instance halves [total][BS]
+  dec::DevBuf<__nv_bfloat16> bgb;          // per-instance factors, CSR order [nnz][BS]
+  dec::DevBuf<double> bb, bx64, br64, bpartial;
   dec::DevBuf<int64_t> crack_buf;          // crack growth: block bests, picked edge
-  int batch_variant[4] = {0, 0, 0, 0};     // tuned gather variant + 1 per stride 8..64
+  int batch_variant[4] = {0, 0, 0, 0};     // tuned variant + 1 per stride 8..64
   int64_t batch_tune_key[4][2] = {};       // (n, nnz) each choice was tuned for
-  int batch_variant_used = -1;             // gather entries of the last batched solve
+  int batch_variant_used = -1;             // variant of the last batched solve
   double batch_kernel_ms = -1.0;           // device time of its persistent launch
-  dec::DevBuf<__nv_bfloat16> bg16, bgb;   // shared factor, per-instance factors
-  bool batch_per_instance = false;
+  int64_t crack_iters = 0;                 // CG iterations of the last crack growth
+  bool batch_per_instance = false;         // per-instance FSAI factors
   dec::DevBuf<float> bx, br, bz, bp, bq, bt;
+  // conductivity fields (dec_hodge_assemble_fields): instances with their
+  // own *1; w then holds [n_fields][ne]
+  int n_fields = 1;
   std::vector<int> iters_host;
   std::vector<double> relres_host;
 
@@ -172,10 +201,13 @@ struct dec_ctx {
     cg.release(); out3.release(); flush.release();
     sellL.release(); sellLo.release(); sellUp.release(); sL64.release();
     sGlo64.release(); sGup64.release(); sL32.release(); sGlo16.release();
-    sGup16.release(); big_rows.release(); coop.release(); bw32.release();
-    bw64.release(); bb.release(); bx64.release(); br64.release(); bpartial.release();
-    bfc.release(); kpartial.release(); crack_buf.release(); bg16.release(); bx.release(); br.release(); bz.release();
-    bp.release(); bq.release(); bt.release(); bgb.release();
+    sGup16.release(); big_rows.release(); coop.release();
+    morton.release(); mrank.release(); bL.release(); bGlo.release(); bGup.release(); bLcw.release();
+    bLfc.release(); bLw.release(); bL64.release(); bd32.release(); bd64.release();
+    bGlo16.release(); bGup16.release(); bGloB.release(); bGupB.release(); bgb.release();
+    bb.release(); bx64.release(); br64.release(); bpartial.release();
+    kpartial.release(); crack_buf.release(); bx.release(); br.release(); bz.release();
+    bp.release(); bq.release(); bt.release();
   }
 
   dec_status fail(dec_status s, const std::string& what) {
@@ -201,6 +233,12 @@ struct dec_ctx {
   } while (0)
 
 namespace dec {
+
+// Operator (value set) of instance `inst`: crack states and conductivity
+// fields each have their own L; Dirichlet value sets share one.
+inline int value_set(const dec_ctx* ctx, int inst) {
+  return (ctx->n_scales > 1 || ctx->n_fields > 1) ? inst : 0;
+}
 
 // Words 2 and 3 of a persistent kernel's barrier: the poll limit of every
 // wait (0 = the default) and whether the last block leaves at once.  Written
@@ -327,30 +365,41 @@ dec_status validate_mesh(dec_ctx* ctx);
 dec_status build_edges(dec_ctx* ctx);
 dec_status build_csr_structure(dec_ctx* ctx);
 dec_status build_sell_layouts(dec_ctx* ctx);
+dec_status build_sell(dec_ctx* ctx, int kind, SellLayout& L, int C, int R,
+                      const int32_t* order);
 template <typename T>
 dec_status scatter_values(dec_ctx* ctx, const SellLayout& L, const double* csr_val, T* out);
 // Hodge
-dec_status assemble_hodge(dec_ctx* ctx, int64_t n_discs, bool has_k);
-dec_status validate_k(dec_ctx* ctx);
+dec_status assemble_hodge(dec_ctx* ctx, int64_t n_discs, bool has_k, int n_fields);
+dec_status validate_k(dec_ctx* ctx, int64_t count);
 // system
 dec_status build_values(dec_ctx* ctx, int inst);
 dec_status build_precond(dec_ctx* ctx, int vs);
 dec_status build_values_uncracked(dec_ctx* ctx);
+// rows and FSAI rows of L changed by cracking edge e (first_cut[e] already 0)
+dec_status crack_update(dec_ctx* ctx, int64_t e);
 // solve
+// warm: start from the current solution u of the instance instead of 0
 dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
-                          int mode, int* iters, double* relres);
+                          int mode, int* iters, double* relres, bool warm = false);
 dec_status k_eff_all(dec_ctx* ctx, double* out3_host);   // [B][3], one pass
 dec_status form_T(dec_ctx* ctx, int inst, double* T);
 dec_status solve_mixed_persistent(dec_ctx* ctx, int inst, double rtol, int max_iter,
                                   int* iters_out, double* relres_out);
 dec_status batch_setup(dec_ctx* ctx);
+// warm: start every instance from the last batched solution
 dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
-                         double* relres);
+                         double* relres, bool warm = false);
+// per-instance values of the batched layouts after per-instance *1 changed
+dec_status batch_refresh_values(dec_ctx* ctx);
 dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
                        double* avg_ms);
 // shared-memory limits of the staged SELL kernels (current device)
 cudaError_t init_kernel_attributes();
 // crack growth
+dec_status crack_paths(dec_ctx* ctx, int P, int max_steps, const int32_t* orders_dev,
+                       double rtol, int max_iter, double k_stop, double* k_eff,
+                       int32_t* steps);
 dec_status crack_evolve(dec_ctx* ctx, int rule, int max_steps, const int32_t* order_host,
                         double rtol, int max_iter, int mode, double k_stop, int32_t* cracked,
                         double* k_eff, int32_t* steps);

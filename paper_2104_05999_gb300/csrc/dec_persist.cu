@@ -372,7 +372,7 @@ pcg_mixed_persistent(PersistArgs a) {
 dec_status solve_mixed_persistent(dec_ctx* ctx, int inst, double rtol, int max_iter,
                                   int* iters_out, double* relres_out) {
   const int64_t n = ctx->n;
-  const int vs = ctx->n_scales > 1 ? inst : 0;
+  const int vs = value_set(ctx, inst);
   cudaStream_t s = ctx->stream;
   const bool fsai = ctx->precond == DEC_PRECOND_FSAI;
   int dev_coop = 0;

@@ -11,7 +11,9 @@
 //
 // Three matrices share the CSR structure of L: L itself, the lower half of
 // the FSAI factor (entries up to the diagonal: G) and the upper half (from the
-// diagonal on: G^T).  Each gets its own permutation, slice pointers and
+// diagonal on: G^T).  The batched solve uses the same builder with slices of
+// C = 32 / (threads per row) rows and windows of R rows taken in a spatial
+// (Morton) order of the nodes instead of the natural one.  Each gets its own permutation, slice pointers and
 // column array; `pos` maps a CSR slot to its SELL slot (-1 if not present),
 // so value arrays built in CSR order are scattered once per build.
 #include "dec_internal.cuh"
@@ -22,112 +24,145 @@ namespace dec {
 
 constexpr int kWindow = 512;
 
-// kind 0: whole row; 1: lower half incl. diagonal; 2: upper half incl. diagonal
-__device__ __forceinline__ void row_range(int kind, const int32_t* rowptr,
-                                          const int32_t* dpos, int64_t i,
-                                          int32_t* k0, int32_t* k1) {
-  if (kind == 0) { *k0 = rowptr[i]; *k1 = rowptr[i + 1]; }
-  else if (kind == 1) { *k0 = rowptr[i]; *k1 = dpos[i] + 1; }
-  else { *k0 = dpos[i]; *k1 = rowptr[i + 1]; }
+// Entries of row i that a layout of `kind` stores, in CSR order:
+//   0: the whole row; 1: lower half incl. diagonal (G); 2: upper half incl.
+//   diagonal (G^T); 3: off-diagonal entries, none on Dirichlet rows (edge
+//   form of the batched solve); 4: off-diagonal entries whose column is not
+//   a Dirichlet node, none on Dirichlet rows (CSR form of the batched solve,
+//   whose Dirichlet columns carry no value).
+__device__ __forceinline__ bool kind_keeps(int kind, int32_t k, int32_t kd, int32_t c,
+                                           const uint8_t* tag) {
+  if (kind == 0) return true;
+  if (kind == 1) return k <= kd;
+  if (kind == 2) return k >= kd;
+  if (kind == 3) return k != kd;
+  return k != kd && tag[c] != DEC_NODE_DIRICHLET;
 }
 
-// rank rows of each 512-row window by (length desc, row asc)
-__global__ void __launch_bounds__(kWindow)
-sell_sort_kernel(int kind, int64_t n, const int32_t* __restrict__ rowptr,
-                 const int32_t* __restrict__ dpos, int32_t* __restrict__ perm,
-                 int32_t* __restrict__ len_out) {
-  __shared__ int32_t len[kWindow];
-  const int64_t row = (int64_t)blockIdx.x * kWindow + threadIdx.x;
-  int32_t l = -1;
-  if (row < n) {
-    int32_t k0, k1;
-    row_range(kind, rowptr, dpos, row, &k0, &k1);
-    l = k1 - k0;
+__device__ __forceinline__ int32_t kind_len(int kind, const int32_t* rowptr,
+                                            const int32_t* dpos, const int32_t* col,
+                                            const uint8_t* tag, int64_t i) {
+  const int32_t k0 = rowptr[i], k1 = rowptr[i + 1], kd = dpos[i];
+  if (kind == 0) return k1 - k0;
+  if (kind == 1) return kd - k0 + 1;
+  if (kind == 2) return k1 - kd;
+  if (tag[i] == DEC_NODE_DIRICHLET) return 0;
+  if (kind == 3) return k1 - k0 - 1;
+  int32_t l = 0;
+  for (int32_t k = k0; k < k1; ++k) l += kind_keeps(4, k, kd, col[k], tag) ? 1 : 0;
+  return l;
+}
+
+// Rank the rows of each window of R rows (natural order, or the order
+// `order` gives) by (length desc, position asc).  One block per window,
+// blockDim = R.
+__global__ void sell_sort_kernel(int kind, int64_t n, const int32_t* __restrict__ order,
+                                 const int32_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ dpos,
+                                 const int32_t* __restrict__ col,
+                                 const uint8_t* __restrict__ tag,
+                                 int32_t* __restrict__ perm, int32_t* __restrict__ len_out) {
+  extern __shared__ int32_t wlen[];
+  const int R = blockDim.x;
+  const int64_t at = (int64_t)blockIdx.x * R + threadIdx.x;
+  int32_t row = -1, l = -1;
+  if (at < n) {
+    row = order ? order[at] : (int32_t)at;
+    l = kind_len(kind, rowptr, dpos, col, tag, row);
   }
-  len[threadIdx.x] = l;
+  wlen[threadIdx.x] = l;
   __syncthreads();
   int rank = 0;
-  for (int j = 0; j < kWindow; ++j) {
-    const int32_t lj = len[j];
+  for (int j = 0; j < R; ++j) {
+    const int32_t lj = wlen[j];
     rank += (lj > l) || (lj == l && j < (int)threadIdx.x);
   }
-  const int64_t slot = (int64_t)blockIdx.x * kWindow + rank;
-  perm[slot] = row < n ? (int32_t)row : -1;
+  const int64_t slot = (int64_t)blockIdx.x * R + rank;
+  perm[slot] = row;
   len_out[slot] = l < 0 ? 0 : l;   // length of the row in slot order
 }
 
-// entries of slice s = 32 * (length of its first, longest row)
-__global__ void sell_width_kernel(int64_t nslices, const int32_t* __restrict__ len_sorted,
+// entries of slice s = C * (length of its first, longest row)
+__global__ void sell_width_kernel(int64_t nslices, int C, const int32_t* __restrict__ len_sorted,
                                   uint32_t* __restrict__ size) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s <= nslices;
        s += (int64_t)gridDim.x * blockDim.x)
-    size[s] = s < nslices ? 32u * (uint32_t)len_sorted[32 * s] : 0u;
+    size[s] = s < nslices ? (uint32_t)C * (uint32_t)len_sorted[(int64_t)C * s] : 0u;
 }
 
-__global__ void sell_fill_kernel(int kind, int64_t nslices,
+__global__ void sell_fill_kernel(int kind, int64_t nslices, int C,
                                  const int32_t* __restrict__ rowptr,
                                  const int32_t* __restrict__ dpos,
                                  const int32_t* __restrict__ csr_col,
+                                 const uint8_t* __restrict__ tag,
                                  const int32_t* __restrict__ perm,
                                  const int32_t* __restrict__ sptr,
                                  int32_t* __restrict__ scol, int32_t* __restrict__ pos) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t s = t >> 5;
-  const int lane = (int)(t & 31);
+  const int64_t s = t / C;
+  const int lane = (int)(t % C);
   if (s >= nslices) return;
-  const int32_t r = perm[32 * s + lane];
+  const int32_t r = perm[t];
   const int32_t base = sptr[s];
-  const int32_t w = (sptr[s + 1] - base) >> 5;
-  int32_t k0 = 0, k1 = 0;
-  if (r >= 0) row_range(kind, rowptr, dpos, r, &k0, &k1);
-  for (int32_t j = 0; j < w; ++j) {
-    const int32_t p = base + 32 * j + lane;
-    if (r >= 0 && j < k1 - k0) {
-      scol[p] = csr_col[k0 + j];
-      pos[k0 + j] = p;
-    } else {
-      scol[p] = r >= 0 ? r : 0;   // padding: value 0, a column already in cache
+  const int32_t w = (sptr[s + 1] - base) / C;
+  int32_t j = 0;
+  if (r >= 0 && !((kind == 3 || kind == 4) && tag[r] == DEC_NODE_DIRICHLET)) {
+    const int32_t kd = dpos[r];
+    for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+      if (!kind_keeps(kind, k, kd, csr_col[k], tag)) continue;
+      const int32_t p = base + C * j + lane;
+      scol[p] = csr_col[k];
+      pos[k] = p;
+      ++j;
     }
   }
+  // padding: value 0, a column already in cache (the row itself)
+  for (; j < w; ++j) scol[base + C * j + lane] = r >= 0 ? r : 0;
 }
 
-dec_status build_sell(dec_ctx* ctx, int kind, SellLayout& L) {
+dec_status build_sell(dec_ctx* ctx, int kind, SellLayout& L, int C, int R,
+                      const int32_t* order) {
   const int64_t n = ctx->n;
   cudaStream_t s = ctx->stream;
-  const int64_t nwin = (n + kWindow - 1) / kWindow;
-  L.nslices = nwin * (kWindow / 32);
-  const int64_t slots = L.nslices * 32;
+  if (C < 1 || R % C != 0 || R > 1024) return ctx->fail(DEC_ERR_ARG, "build_sell: bad shape");
+  const int64_t nwin = (n + R - 1) / R;
+  L.C = C;
+  L.R = R;
+  L.nslices = nwin * (R / C);
+  const int64_t slots = nwin * R;
   DEC_TRY(L.perm.ensure(slots));
   DEC_TRY(L.len.ensure(slots));
   DEC_TRY(L.sptr.ensure(L.nslices + 1));
   DEC_TRY(L.pos.ensure(ctx->nnz));
-  sell_sort_kernel<<<(unsigned)nwin, kWindow, 0, s>>>(kind, n, ctx->rowptr.p, ctx->dpos.p,
-                                                     L.perm.p, L.len.p);
+  sell_sort_kernel<<<(unsigned)nwin, R, R * sizeof(int32_t), s>>>(
+      kind, n, order, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, ctx->tag.p, L.perm.p, L.len.p);
   sell_width_kernel<<<(unsigned)std::min<int64_t>((L.nslices + 256) / 256, 4096), 256, 0, s>>>(
-      L.nslices, L.len.p, (uint32_t*)L.sptr.p);
+      L.nslices, C, L.len.p, (uint32_t*)L.sptr.p);
   DEC_TRY(cudaGetLastError());
   DEC_TRY(ctx->scan_tmp.ensure(scan_tmp_size(L.nslices + 1)));
   DEC_TRY(exclusive_scan_u32((const uint32_t*)L.sptr.p, (uint32_t*)L.sptr.p, L.nslices + 1,
                              ctx->scan_tmp.p, ctx->scan_tmp.cap, s));
-  int32_t total = 0;
-  DEC_TRY(cudaMemcpyAsync(&total, L.sptr.p + L.nslices, sizeof(int32_t),
+  uint32_t total = 0;
+  DEC_TRY(cudaMemcpyAsync(&total, L.sptr.p + L.nslices, sizeof(uint32_t),
                           cudaMemcpyDeviceToHost, s));
   DEC_TRY(cudaStreamSynchronize(s));
+  if (total >= (uint32_t)INT32_MAX)
+    return ctx->fail(DEC_ERR_LIMIT, "sliced layout: more than 2^31 - 1 entries");
   L.total = total;
   DEC_TRY(L.col.ensure(total));
   DEC_TRY(cudaMemsetAsync(L.pos.p, 0xff, sizeof(int32_t) * ctx->nnz, s));
   sell_fill_kernel<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(
-      kind, L.nslices, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, L.perm.p, L.sptr.p,
-      L.col.p, L.pos.p);
+      kind, L.nslices, C, ctx->rowptr.p, ctx->dpos.p, ctx->col.p, ctx->tag.p, L.perm.p,
+      L.sptr.p, L.col.p, L.pos.p);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 6;  // sort, widths, scan (3), fill
   return DEC_OK;
 }
 
 dec_status build_sell_layouts(dec_ctx* ctx) {
-  DEC_TRY_STATUS(build_sell(ctx, 0, ctx->sellL));
-  DEC_TRY_STATUS(build_sell(ctx, 1, ctx->sellLo));
-  DEC_TRY_STATUS(build_sell(ctx, 2, ctx->sellUp));
+  DEC_TRY_STATUS(build_sell(ctx, 0, ctx->sellL, 32, kWindow, nullptr));
+  DEC_TRY_STATUS(build_sell(ctx, 1, ctx->sellLo, 32, kWindow, nullptr));
+  DEC_TRY_STATUS(build_sell(ctx, 2, ctx->sellUp, 32, kWindow, nullptr));
   return DEC_OK;
 }
 

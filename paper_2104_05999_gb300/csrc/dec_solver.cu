@@ -53,6 +53,45 @@ cg_init_kernel(int64_t n, const BT* __restrict__ b, VT* __restrict__ x,
   }
 }
 
+// Scalars of an FP64 CG that starts from x0 != 0 (a warm start): the
+// residual r = b - L x0 and its r.r (*rr_in) are already computed; here
+// |b|^2 (the stopping rule stays ||b - L x|| <= rtol ||b||), p = 0.
+__global__ void __launch_bounds__(kBlock)
+cg_warm_init_kernel(int64_t n, const double* __restrict__ b, double* __restrict__ p,
+                    double rtol2, const double* __restrict__ rr_in, CgScalars* cg,
+                    double* partial, unsigned* ticket) {
+  double bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    bb += b[i] * b[i];
+    p[i] = 0.0;
+  }
+  double v[1] = {bb}, t[1];
+  if (grid_reduce<kBlock, 1>(v, t, partial, ticket) && threadIdx.x == 0) {
+    const double rr = *rr_in;
+    cg->bnorm2 = t[0];
+    cg->tol2 = rtol2 * t[0];
+    cg->rr = rr;
+    cg->done = (t[0] == 0.0 || rr <= rtol2 * t[0]) ? 1 : 0;
+    cg->iters = 0;
+    cg->breakdown = 0;
+    cg->beta = 0.0;
+    cg->rz = 0.0;
+  }
+}
+
+// *out = |b|^2
+__global__ void __launch_bounds__(kBlock)
+sq_norm_kernel(int64_t n, const double* __restrict__ b, double* out, double* partial,
+               unsigned* ticket) {
+  double bb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bb += b[i] * b[i];
+  double v[1] = {bb}, t[1];
+  if (grid_reduce<kBlock, 1>(v, t, partial, ticket) && threadIdx.x == 0) *out = t[0];
+}
+
 // Widths (entries per row) staged in shared memory by the SELL kernels.
 // The FSAI halves (at most 14 entries per row on the Delaunay meshes here)
 // are staged: their BF16 apply ran 1.3-1.5x faster than with register
@@ -394,13 +433,14 @@ __global__ void __launch_bounds__(kBlock)
 k_eff_batch_kernel(int64_t n, const int32_t* __restrict__ rowptr,
                    const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
                    const int32_t* __restrict__ dpos, const uint8_t* __restrict__ tag,
-                   const double* __restrict__ xyz, const double* __restrict__ w,
-                   const uint8_t* __restrict__ fc, int states, int sets,
-                   const double* __restrict__ u, const double* __restrict__ T0,
+                   const double* __restrict__ xyz, const double* __restrict__ w0,
+                   int64_t ne, const uint8_t* __restrict__ fc, int states, int sets,
+                   int fields, const double* __restrict__ u, const double* __restrict__ T0,
                    double* __restrict__ partial) {
   __shared__ double sh[kBlock];
   const int b = blockIdx.y;
   const int state = states ? b : 0;
+  const double* w = w0 + (fields ? (int64_t)b * ne : 0);   // this instance's *1
   const double* ub = u + (int64_t)b * n;
   const double* t0 = T0 + (sets ? (int64_t)b * n : 0);
   auto Tof = [&](int64_t i) { return ub[i] + (tag[i] == DEC_NODE_DIRICHLET ? t0[i] : 0.0); };
@@ -454,11 +494,11 @@ dec_status k_eff_all(dec_ctx* ctx, double* out3_host) {
       1, std::min<int64_t>((n + kBlock - 1) / kBlock,
                            (int64_t)ctx->num_sms * (B >= 8 ? 1 : 4)));
   DEC_TRY(ctx->kpartial.ensure((size_t)3 * B * G));
-  DEC_TRY(ctx->out3.ensure(3 * (size_t)B + 1));
+  DEC_TRY(ctx->out3.ensure(3 * (size_t)B + 2));
   k_eff_batch_kernel<<<dim3(G, (unsigned)B), kBlock, 0, s>>>(
       n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->xyz.p, ctx->w.p,
-      ctx->first_cut.p, ctx->n_scales > 1, ctx->n_sets > 1, ctx->u.p, ctx->T0.p,
-      ctx->kpartial.p);
+      ctx->ne, ctx->first_cut.p, ctx->n_scales > 1, ctx->n_sets > 1, ctx->n_fields > 1,
+      ctx->u.p, ctx->T0.p, ctx->kpartial.p);
   k_eff_batch_sum_kernel<<<(unsigned)((3 * B + 3) / 4), 128, 0, s>>>(
       (int)G, 3 * B, ctx->kpartial.p, ctx->out3.p);
   DEC_TRY(cudaGetLastError());
@@ -571,9 +611,9 @@ static dec_status run_pcg(dec_ctx* ctx, int64_t n, const Ops<MT, PT, DT>& op, VT
 }
 
 dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
-                          int mode, int* iters_out, double* relres_out) {
+                          int mode, int* iters_out, double* relres_out, bool warm) {
   const int64_t n = ctx->n;
-  const int vs = ctx->n_scales > 1 ? inst : 0;
+  const int vs = value_set(ctx, inst);
   cudaStream_t s = ctx->stream;
   const unsigned G = (unsigned)ctx->grid_vec, Gs = (unsigned)ctx->grid_sell;
   const SellArg<double> A64 = sell_arg(ctx->sellL, ctx->sL64.p + (int64_t)vs * ctx->sellL.total);
@@ -594,10 +634,20 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
         fsai ? nullptr : ctx->dinv64.p + (int64_t)vs * n};
     double *x = ctx->x64.p, *r = ctx->r64.p, *z = ctx->z64.p, *p = ctx->p64.p,
            *q = ctx->q64.p, *t = ctx->t64.p;
-    ctx->launches += 1;
-    cg_init_kernel<double, double><<<G, kBlock, 0, s>>>(n, bvec, x, r, p, rtol * rtol,
-                                                        ctx->cg.p, ctx->partial.p,
-                                                        ctx->ticket.p);
+    if (warm) {
+      // start from the current solution u: r = b - L u
+      DEC_TRY(cudaMemcpyAsync(x, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      ctx->launches += 2;
+      residual_kernel<<<Gs, kBlock, 0, s>>>(A64, x, bvec, r, nullptr, rr_dev, ctx->partial.p,
+                                           ctx->ticket.p);
+      cg_warm_init_kernel<<<G, kBlock, 0, s>>>(n, bvec, p, rtol * rtol, rr_dev, ctx->cg.p,
+                                               ctx->partial.p, ctx->ticket.p);
+    } else {
+      ctx->launches += 1;
+      cg_init_kernel<double, double><<<G, kBlock, 0, s>>>(n, bvec, x, r, p, rtol * rtol,
+                                                          ctx->cg.p, ctx->partial.p,
+                                                          ctx->ticket.p);
+    }
     launch_restart<double>(ctx, n, op, r, z, p, t);
     DEC_TRY(cudaGetLastError());
     for (;;) {
@@ -622,7 +672,7 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
       DEC_TRY(cudaGetLastError());
     }
     DEC_TRY(cudaMemcpyAsync(u, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  } else if (mode == DEC_MODE_MIXED && n <= kPersistMaxRows &&
+  } else if (mode == DEC_MODE_MIXED && !warm && n <= kPersistMaxRows &&
              (st = solve_mixed_persistent(ctx, inst, rtol, max_iter, iters_out, relres_out)) !=
                  DEC_ERR_LIMIT) {
     return st;   // the whole mixed solve ran as one cooperative kernel
@@ -644,18 +694,25 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
     double* r64 = ctx->r64.p;
     float *x = ctx->x32.p, *r = ctx->r32.p, *z = ctx->z32.p, *p = ctx->p32.p,
           *q = ctx->q32.p, *t = ctx->t32.p;
-    DEC_TRY(cudaMemsetAsync(x64, 0, sizeof(double) * n, s));
-    // r64 = b, r32 = (float) b, |b|^2; the FP32 state starts from r32
+    // x64 = 0 (or the current solution u for a warm start)
+    if (warm) DEC_TRY(cudaMemcpyAsync(x64, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else DEC_TRY(cudaMemsetAsync(x64, 0, sizeof(double) * n, s));
+    // r64 = b - L x64, r32 = (float) r64, |r|^2; the FP32 state starts from r32
     ctx->launches += 2;
     residual_kernel<<<Gs, kBlock, 0, s>>>(A64, x64, bvec, r64, q, rr_dev, ctx->partial.p,
                                          ctx->ticket.p);
     cg_init_kernel<float, float><<<G, kBlock, 0, s>>>(n, q, x, r, p, kSegment, ctx->cg.p,
                                                       ctx->partial.p, ctx->ticket.p);
-    DEC_TRY(cudaMemcpyAsync(&bnorm2, rr_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DEC_TRY(cudaMemcpyAsync(&rr_true, rr_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (warm) {
+      ctx->launches += 1;
+      sq_norm_kernel<<<G, kBlock, 0, s>>>(n, bvec, rr_dev + 1, ctx->partial.p, ctx->ticket.p);
+      DEC_TRY(cudaMemcpyAsync(&bnorm2, rr_dev + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     launch_restart<float>(ctx, n, op, r, z, p, t, 1);
     DEC_TRY(cudaGetLastError());
     DEC_TRY(cudaStreamSynchronize(s));
-    rr_true = bnorm2;
+    if (!warm) bnorm2 = rr_true;
     double best = rr_true;
     int stall = 0;
     while (bnorm2 > 0.0 && rr_true > rtol * rtol * bnorm2) {

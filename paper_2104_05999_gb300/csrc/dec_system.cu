@@ -14,9 +14,46 @@ __device__ __forceinline__ double edge_weight(const double* w, const uint8_t* fc
   return (int)fc[e] > state ? w[e] : 0.0;
 }
 
-// One thread per row.  Off-diagonal -w_ij (0 towards Dirichlet nodes, whose
+// Row i of L and b.  Off-diagonal -w_ij (0 towards Dirichlet nodes, whose
 // values move to b), diagonal sum_j w_ij; Dirichlet rows and rows with all
 // weights zero become identity rows with b = 0.
+__device__ __forceinline__ void laplacian_row(
+    int64_t i, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const int32_t* __restrict__ eid, const int32_t* __restrict__ dpos,
+    const uint8_t* __restrict__ tag, const double* __restrict__ w,
+    const uint8_t* __restrict__ fc, int state, const double* __restrict__ T0,
+    double* __restrict__ val, double* __restrict__ b) {
+  const int32_t k0 = rowptr[i], k1 = rowptr[i + 1], kd = dpos[i];
+  if (tag[i] == DEC_NODE_DIRICHLET) {
+    for (int32_t k = k0; k < k1; ++k) val[k] = k == kd ? 1.0 : 0.0;
+    b[i] = 0.0;
+    return;
+  }
+  double diag = 0.0, bi = 0.0;
+  for (int32_t k = k0; k < k1; ++k) {
+    if (k == kd) continue;
+    const double we = edge_weight(w, fc, eid[k], state);
+    diag += we;
+    const int32_t j = col[k];
+    double v;
+    if (tag[j] == DEC_NODE_DIRICHLET) {
+      v = 0.0;
+      bi += we * T0[j];
+    } else {
+      v = we == 0.0 ? 0.0 : -we;
+    }
+    val[k] = v;
+  }
+  if (diag == 0.0) {  // isolated by cracks: decoupled identity row
+    val[kd] = 1.0;
+    b[i] = 0.0;
+  } else {
+    val[kd] = diag;
+    b[i] = bi;
+  }
+}
+
+// One thread per row.
 __global__ void laplacian_values_kernel(
     int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const int32_t* __restrict__ eid, const int32_t* __restrict__ dpos,
@@ -24,36 +61,8 @@ __global__ void laplacian_values_kernel(
     const uint8_t* __restrict__ fc, int state, const double* __restrict__ T0,
     double* __restrict__ val, double* __restrict__ b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t k0 = rowptr[i], k1 = rowptr[i + 1], kd = dpos[i];
-    if (tag[i] == DEC_NODE_DIRICHLET) {
-      for (int32_t k = k0; k < k1; ++k) val[k] = k == kd ? 1.0 : 0.0;
-      b[i] = 0.0;
-      continue;
-    }
-    double diag = 0.0, bi = 0.0;
-    for (int32_t k = k0; k < k1; ++k) {
-      if (k == kd) continue;
-      const double we = edge_weight(w, fc, eid[k], state);
-      diag += we;
-      const int32_t j = col[k];
-      double v;
-      if (tag[j] == DEC_NODE_DIRICHLET) {
-        v = 0.0;
-        bi += we * T0[j];
-      } else {
-        v = we == 0.0 ? 0.0 : -we;
-      }
-      val[k] = v;
-    }
-    if (diag == 0.0) {  // isolated by cracks: decoupled identity row
-      val[kd] = 1.0;
-      b[i] = 0.0;
-    } else {
-      val[kd] = diag;
-      b[i] = bi;
-    }
-  }
+       i += (int64_t)gridDim.x * blockDim.x)
+    laplacian_row(i, rowptr, col, eid, dpos, tag, w, fc, state, T0, val, b);
 }
 
 __global__ void jacobi_kernel(int64_t n, const int32_t* __restrict__ dpos,
@@ -284,13 +293,14 @@ static unsigned grid_rows(const dec_ctx* ctx, int64_t work, int per_block) {
 
 dec_status build_values(dec_ctx* ctx, int inst) {
   const int64_t n = ctx->n, nnz = ctx->nnz;
-  const int vs = ctx->n_scales > 1 ? inst : 0;      // value set
+  const int vs = value_set(ctx, inst);               // value set
   const int ts = ctx->n_sets > 1 ? inst : 0;        // Dirichlet set
+  const int fs = ctx->n_fields > 1 ? inst : 0;      // conductivity field
   double* val = ctx->val64.p + (int64_t)vs * nnz;
   laplacian_values_kernel<<<grid_rows(ctx, n, 256), 256, 0, ctx->stream>>>(
-      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->w.p,
-      ctx->first_cut.p, ctx->n_scales > 1 ? inst : 0, ctx->T0.p + (int64_t)ts * n,
-      val, ctx->b.p + (int64_t)inst * n);
+      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p,
+      ctx->w.p + (int64_t)fs * ctx->ne, ctx->first_cut.p, ctx->n_scales > 1 ? inst : 0,
+      ctx->T0.p + (int64_t)ts * n, val, ctx->b.p + (int64_t)inst * n);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 1;
   if (inst == vs) {   // first instance of this value set: solver copies
@@ -358,6 +368,114 @@ dec_status build_precond(dec_ctx* ctx, int vs) {
   DEC_TRY(cudaStreamSynchronize(s));
   if (flag & 8)
     return ctx->fail(DEC_ERR_LIMIT, "an FSAI row has more than 32 lower-pattern entries");
+  return DEC_OK;
+}
+
+// ------------------------------------------------------ crack update
+// A crack sets the *1 of one edge e = (i, j) to 0 (Sec. 2.3, 2.5): only rows
+// and columns i and j of L change (L_ii, L_jj, L_ij, L_ji, plus b_i, b_j
+// through Dirichlet neighbours).  Threads 0 and 1 recompute rows i and j
+// exactly as a full build does, with their solver copies and Jacobi entries;
+// thread 0 then lists the FSAI rows whose principal block L[P_r, P_r] holds
+// i or j (P_r = lower pattern of row r): r = i, j and their neighbours of
+// larger id.
+__global__ void crack_rows_kernel(int64_t e, const int32_t* __restrict__ E,
+                                  const int32_t* __restrict__ rowptr,
+                                  const int32_t* __restrict__ col,
+                                  const int32_t* __restrict__ eid,
+                                  const int32_t* __restrict__ dpos,
+                                  const uint8_t* __restrict__ tag, const double* __restrict__ w,
+                                  const uint8_t* __restrict__ fc, const double* __restrict__ T0,
+                                  double* __restrict__ val, double* __restrict__ b,
+                                  const int32_t* __restrict__ sell_pos, double* __restrict__ sL64,
+                                  float* __restrict__ sL32, double* __restrict__ dinv64,
+                                  float* __restrict__ dinv32, int32_t* __restrict__ list,
+                                  int32_t* __restrict__ count) {
+  if (threadIdx.x < 2) {
+    const int64_t i = E[2 * e + threadIdx.x];
+    laplacian_row(i, rowptr, col, eid, dpos, tag, w, fc, 0, T0, val, b);
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int32_t p = sell_pos[k];
+      if (p >= 0) {
+        sL64[p] = val[k];
+        sL32[p] = (float)val[k];
+      }
+    }
+    if (dinv64) {
+      const double d = 1.0 / val[dpos[i]];
+      dinv64[i] = d;
+      dinv32[i] = (float)d;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t c = 0;
+    for (int h = 0; h < 2; ++h) {
+      const int32_t i = E[2 * e + h];
+      list[c++] = i;
+      for (int32_t k = dpos[i] + 1; k < rowptr[i + 1]; ++k) list[c++] = col[k];
+    }
+    *count = c;
+  }
+}
+
+// solver copies (FP64 and BF16, both halves) of the listed FSAI rows
+__global__ void fsai_rows_scatter_kernel(const int32_t* __restrict__ list,
+                                         const int32_t* __restrict__ count,
+                                         const int32_t* __restrict__ rowptr,
+                                         const int32_t* __restrict__ dpos,
+                                         const int32_t* __restrict__ eid,
+                                         const int32_t* __restrict__ pos_up,
+                                         const double* __restrict__ g64,
+                                         const int32_t* __restrict__ lo_pos,
+                                         const int32_t* __restrict__ up_pos,
+                                         double* __restrict__ glo64, double* __restrict__ gup64,
+                                         __nv_bfloat16* __restrict__ glo16,
+                                         __nv_bfloat16* __restrict__ gup16) {
+  const int32_t nrows = *count;
+  for (int32_t li = threadIdx.x; li < nrows; li += blockDim.x) {
+    const int32_t r = list[li];
+    for (int32_t k = rowptr[r]; k <= dpos[r]; ++k) {
+      const double g = g64[k];
+      const int32_t pl = lo_pos[k];
+      if (pl >= 0) {
+        glo64[pl] = g;
+        glo16[pl] = __float2bfloat16_rn((float)g);
+      }
+      const int32_t tp = k == dpos[r] ? k : pos_up[eid[k]];
+      const int32_t pu = up_pos[tp];
+      if (pu >= 0) {
+        gup64[pu] = g64[tp];
+        gup16[pu] = __float2bfloat16_rn((float)g64[tp]);
+      }
+    }
+  }
+}
+
+dec_status crack_update(dec_ctx* ctx, int64_t e) {
+  cudaStream_t s = ctx->stream;
+  const bool jac = ctx->precond == DEC_PRECOND_JACOBI;
+  // the list holds at most 2 + deg(i) + deg(j) <= nnz rows
+  DEC_TRY(ctx->big_rows.ensure(ctx->nnz + 1));
+  int32_t* list = ctx->big_rows.p;
+  int32_t* count = ctx->big_rows.p + ctx->nnz;
+  crack_rows_kernel<<<1, 32, 0, s>>>(
+      e, ctx->E.p, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->w.p,
+      ctx->first_cut.p, ctx->T0.p, ctx->val64.p, ctx->b.p, ctx->sellL.pos.p, ctx->sL64.p,
+      ctx->sL32.p, jac ? ctx->dinv64.p : nullptr, jac ? ctx->dinv32.p : nullptr, list, count);
+  DEC_TRY(cudaGetLastError());
+  ctx->launches += 1;
+  if (jac) return DEC_OK;
+  DEC_TRY(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
+  fsai_setup_list_kernel<<<16, 32 * kFsaiWarps, 0, s>>>(
+      list, count, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->pos_up.p,
+      ctx->val64.p, ctx->g64.p, ctx->errflag.p);
+  fsai_rows_scatter_kernel<<<1, 64, 0, s>>>(
+      list, count, ctx->rowptr.p, ctx->dpos.p, ctx->eid.p, ctx->pos_up.p, ctx->g64.p,
+      ctx->sellLo.pos.p, ctx->sellUp.pos.p, ctx->sGlo64.p, ctx->sGup64.p, ctx->sGlo16.p,
+      ctx->sGup16.p);
+  DEC_TRY(cudaGetLastError());
+  ctx->launches += 2;
   return DEC_OK;
 }
 

@@ -24,10 +24,16 @@ def run_path(ctx: abi.Context, xyz, tets, tags, T0, k=None, discs=None,
              scales=None, precond="fsai", mode="fp64", rtol=1e-10,
              max_iter=100000, want_T=True, raise_on_error=True) -> PathResult:
     """Run every step of the path on one mesh; inputs may be numpy arrays or
-    torch CUDA tensors.  Returns iteration counts, residuals, k_eff pieces
+    torch CUDA tensors.  ``k`` is one per-tet field [n_tets] or a stack of
+    fields [n_fields, n_tets] (one instance per field).  Returns iteration counts, residuals, k_eff pieces
     and (optionally) the temperature field of every instance."""
     ctx.dec_mesh_upload(xyz, tets, tags)
-    ctx.dec_hodge_assemble(k, discs, scales)
+    if k is not None and len(k.shape) == 2:       # several conductivity fields
+        if scales is not None:
+            raise ValueError("conductivity fields and crack states at once")
+        ctx.dec_hodge_assemble_fields(k, discs)
+    else:
+        ctx.dec_hodge_assemble(k, discs, scales)
     pc = {"fsai": abi.DEC_PRECOND_FSAI, "jacobi": abi.DEC_PRECOND_JACOBI,
           "fsai_shared": abi.DEC_PRECOND_FSAI_SHARED}[precond]
     if mode == "batched":

@@ -63,3 +63,28 @@ def test_reference_arm_prints_on_rank_zero_only(rank, prints, tmp_path):
     if prints:
         d = json.loads(lines[0])
         assert d["impl"] == "reference" and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def _shard_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port),
+                      RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ids = bench.rank_instances(3, rank, world)
+        # stand-in for this rank's batched solve: k_eff of instance i
+        k_local = [100.0 + i for i in ids]
+        out[rank] = (ids, bench.gather_instances(k_local, world, "cpu").tolist())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_instances_split_across_two_gloo_ranks_and_gather_in_order():
+    # 6 independent instances on 2 ranks: 3 + 3, k_eff gathered in global order
+    world = 2
+    out = mp.get_context("spawn").Manager().dict()
+    mp.start_processes(_shard_main, args=(world, _free_port(), out), nprocs=world,
+                       join=True, start_method="spawn")
+    assert out[0][0] == [0, 1, 2] and out[1][0] == [3, 4, 5]
+    assert out[0][1] == out[1][1] == [100.0, 101.0, 102.0, 103.0, 104.0, 105.0]
