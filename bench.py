@@ -424,6 +424,9 @@ def gpu_arm(args, rank, world):
         "e2e": {"value": round(statistics.mean(e_times), 4), "unit": "ms",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(round(launches)),
+        "batch_variant": ctx.dec_get_batch_variant() if want == "batched" else None,
+        "batch_phase_ms": ([round(float(x), 4) for x in ctx.dec_get_batch_phase_ms()]
+                           if want == "batched" else None),
         "clocks": clocks,
     }
     ctx.close()

@@ -216,8 +216,10 @@ dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy);
  * (nodes, matrix entries) at each instance stride (8, 16, 32, 64) times a
  * few iterations of every variant and keeps the fastest for the context's
  * later solves of that size.
- *   gather_entries  host: matrix entries whose neighbour rows a thread
- *                   gathers per round trip (2, 4 or 8).
+ *   gather_entries  host: 100 * (gathers into shared memory by cp.async)
+ *                   + 10 * (next entries' structure loaded while the
+ *                   gathers are in flight) + matrix entries per round trip:
+ *                   one of 2, 4, 12, 114, 106.
  * All variants give bit-identical results.  DEC_ERR_STATE before the first
  * batched solve.  (No counterpart in the paper: a launch-shape choice.) */
 dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries);
@@ -228,6 +230,15 @@ dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries);
  * context's stream around that launch.  DEC_ERR_STATE before the first
  * batched solve.  (No counterpart in the paper: a measurement aid.) */
 dec_status dec_get_batch_kernel_ms(dec_ctx* ctx, double* ms);
+
+/* Where the last batched solve spent a full FP32 iteration, in ms per
+ * iteration (device time read at the grid barriers by one thread of block
+ * 0, averaged over the iterations that ran all five phases): ms5[0] the
+ * sparse matrix - multiple vector product and p.q, [1] the x and r updates
+ * and r.r, [2] the lower FSAI half t = G r, [3] the upper half z = G^T t and
+ * r.z, [4] the p update.  DEC_ERR_STATE before the first batched solve.
+ * (No counterpart in the paper: a measurement aid.) */
+dec_status dec_get_batch_phase_ms(dec_ctx* ctx, double* ms5);
 
 /* crack rules (dec_crack_evolve) */
 enum {

@@ -55,6 +55,7 @@ SIGNATURES = {
     "dec_crack_evolve": [_P, _I32, _I32, _P, _D, _I32, _I32, _D, _P, _P, _P],
     "dec_get_batch_variant": [_P, _P],
     "dec_get_batch_kernel_ms": [_P, _P],
+    "dec_get_batch_phase_ms": [_P, _P],
     "dec_get_crack_iterations": [_P, _P],
     "dec_crack_paths": [_P, _I32, _I32, _P, _D, _I32, _D, _P, _P],
     "dec_get_sizes": [_P, _P, _P, _P, _P, _P],
@@ -248,6 +249,13 @@ class Context:
         v = C.c_int64()
         self._check(self.lib.dec_get_crack_iterations(self.h, C.byref(v)))
         return v.value
+
+    def dec_get_batch_phase_ms(self):
+        """ms per FP32 iteration of the last batched solve's five phases
+        (SpMM, x/r update, FSAI lower, FSAI upper, p update)."""
+        v = np.zeros(5)
+        self._check(self.lib.dec_get_batch_phase_ms(self.h, v.ctypes.data))
+        return v
 
     def dec_get_batch_kernel_ms(self):
         """Device time (ms) of the last batched solve's persistent launch."""

@@ -523,6 +523,16 @@ dec_status dec_get_crack_iterations(const dec_ctx* ctx, int64_t* iters) {
   return DEC_OK;
 }
 
+dec_status dec_get_batch_phase_ms(dec_ctx* ctx, double* ms5) {
+  if (!ctx || !ms5) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->batch_kernel_ms < 0.0)
+    return ctx->fail(DEC_ERR_STATE, "get_batch_phase_ms: no batched solve yet");
+  const double it = ctx->batch_phase_ms[5] > 0.0 ? ctx->batch_phase_ms[5] : 1.0;
+  for (int k = 0; k < 5; ++k) ms5[k] = ctx->batch_phase_ms[k] / it;
+  return DEC_OK;
+}
+
 dec_status dec_get_batch_kernel_ms(dec_ctx* ctx, double* ms) {
   if (!ctx || !ms) return DEC_ERR_ARG;
   ctx->err.clear();

@@ -88,7 +88,31 @@ struct BatchArgs {
   double rtol2, seg2;
   int max_iter;
   int warm;                               // start from x64 (the last solution)
+  double* phase;                          // [6] per-phase device time, block 0
+  int64_t Ltotal, Gtotal[2];              // entries of the sliced layouts
 };
+
+// Bulk prefetch of [p, p + bytes) into L2 by the copy engine (TMA),
+// clipped to [lo, hi) and widened to 16-byte boundaries inside it.  A hint:
+// nothing waits for it.
+__device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes, const void* lo,
+                                            const void* hi) {
+  uintptr_t a = (uintptr_t)p, e = a + bytes;
+  const uintptr_t l = ((uintptr_t)lo + 15) & ~(uintptr_t)15, h = (uintptr_t)hi & ~(uintptr_t)15;
+  a &= ~(uintptr_t)15;
+  e = (e + 15) & ~(uintptr_t)15;
+  if (a < l) a = l;
+  if (e > h) e = h;
+  if (e <= a) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a))
+               : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ bool bgrid_sync(unsigned* bar, int* err) {
   __syncthreads();
@@ -177,87 +201,132 @@ __device__ __forceinline__ void set4(float4& v, int j, float x) {
 
 // ---------------------------------------------------------- row products
 // Lane (r, q) of a warp works on row slot r of the warp's slice and on the
-// instances 4q..4q+3.  Entries are taken U at a time: U coalesced structure
-// loads, then U independent 16-byte gathers, then the FMAs.  The slice
-// width is uniform across the warp, so the guards never diverge; padding
-// entries carry value 0 and the row's own column.
+// instances 4q..4q+3.  Entries are taken U at a time: their structure
+// (coalesced loads), then U independent 16-byte gathers of neighbour rows,
+// then the FMAs; the structure of the next U entries is loaded while the
+// gathers are in flight.  The gathers go to registers, or (SMEM variants)
+// to per-thread shared-memory slots by 16-byte cp.async, which takes no
+// registers while in flight.  The slice width is uniform across the warp,
+// so the guards never diverge; padding entries carry value 0 and the row's
+// own column.
+
+__device__ __forceinline__ float4* gather_slots() {
+  extern __shared__ __align__(16) float4 bsm_slots[];
+  return bsm_slots + threadIdx.x;
+}
+__device__ __forceinline__ void gather_async(float4* slot, const float4* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(slot);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void gather_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+template <int U>
+constexpr int gather_smem() { return U * kBBlock * (int)sizeof(float4); }
+
+// Structure of one L entry: column and its raw weight data (value bits;
+// for crack states also the first crack state; for fields the four
+// instances' weights).
+template <int KIND>
+struct LEnt {
+  int32_t c;
+  float w[KIND == kFields ? kIPT : 1];
+  int f;
+};
+template <int KIND>
+__device__ __forceinline__ LEnt<KIND> l_load(const BatchArgs& a, int64_t p, bool ok, int32_t rr,
+                                             int q) {
+  LEnt<KIND> e;
+  e.f = 0;
+  if constexpr (KIND == kFields) {
+    e.c = ok ? __ldg(a.Lcol + p) : rr;
+    const float4 w4 = ok ? __ldg(reinterpret_cast<const float4*>(a.Lw + p * a.BS) + q)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    e.w[0] = w4.x; e.w[1] = w4.y; e.w[2] = w4.z; e.w[3] = w4.w;
+  } else {
+    const int2 cw = ok ? __ldg(a.Lcw + p) : make_int2(rr, 0);
+    e.c = cw.x;
+    e.w[0] = __int_as_float(cw.y);
+    if constexpr (KIND == kStates) e.f = ok ? (int)__ldg(a.Lfc + p) : 0;
+  }
+  return e;
+}
+// weight of entry e for instance jj of the lane's quad
+template <int KIND>
+__device__ __forceinline__ float l_weight(const LEnt<KIND>& e, int jj, const int (&st)[kIPT]) {
+  if constexpr (KIND == kFields) return e.w[jj];
+  else if constexpr (KIND == kStates) return e.f > st[jj] ? e.w[0] : 0.0f;
+  else return e.w[0];
+}
 
 // (L_b x)_i, FP32, for the four instances of lane (r, q)
-template <int KIND, int U>
-__device__ __forceinline__ float4 l_row(const BatchArgs& a, int64_t s, int r, int q,
-                                        int32_t row, const int (&st)[kIPT],
+template <int KIND, int U, bool SMEM, bool PIPE>
+__device__ __forceinline__ float4 l_row(const BatchArgs& a, int32_t base, int32_t W, int r,
+                                        int q, int32_t row, const int (&st)[kIPT],
                                         const float4* __restrict__ X) {
   const int C = a.C, TPR = a.TPR;
-  const int32_t base = a.Lsptr[s];
-  const int32_t W = (a.Lsptr[s + 1] - base) / C;
   const int32_t rr = row >= 0 ? row : 0;
   const float4 xi = X[(int64_t)rr * TPR + q];
-  if constexpr (KIND == kSets) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int32_t j = 0; j < W; j += U) {
-      int2 e[U];
-      float4 xv[U];
+  float4* slots = gather_slots();
+  float acc[kIPT] = {0.f, 0.f, 0.f, 0.f}, dsum[kIPT] = {0.f, 0.f, 0.f, 0.f};
+  LEnt<KIND> e[U];
+  if constexpr (PIPE) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        e[u] = j + u < W ? __ldg(a.Lcw + base + C * (j + u) + r) : make_int2(rr, 0);
+    for (int u = 0; u < U; ++u) e[u] = l_load<KIND>(a, base + C * u + r, u < W, rr, q);
+  }
+  for (int32_t j = 0; j < W; j += U) {
+    if constexpr (!PIPE) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        xv[u] = j + u < W ? X[(int64_t)e[u].x * TPR + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < U; ++u) e[u] = l_load<KIND>(a, base + C * (j + u) + r, j + u < W, rr, q);
+    }
+    float4 xv[SMEM ? 1 : U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (j + u < W) {
-          const float v = __int_as_float(e[u].y);
-          acc.x = fmaf(v, xv[u].x, acc.x);
-          acc.y = fmaf(v, xv[u].y, acc.y);
-          acc.z = fmaf(v, xv[u].z, acc.z);
-          acc.w = fmaf(v, xv[u].w, acc.w);
-        }
+    for (int u = 0; u < U; ++u) {
+      if constexpr (SMEM) {
+        if (j + u < W) gather_async(slots + u * kBBlock, X + (int64_t)e[u].c * TPR + q);
+      } else {
+        xv[u] = j + u < W ? X[(int64_t)e[u].c * TPR + q] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    const float d = a.d32[rr];
-    return make_float4(fmaf(d, xi.x, acc.x), fmaf(d, xi.y, acc.y), fmaf(d, xi.z, acc.z),
-                       fmaf(d, xi.w, acc.w));
-  } else {
-    float acc[kIPT] = {0.f, 0.f, 0.f, 0.f}, dsum[kIPT] = {0.f, 0.f, 0.f, 0.f};
-    for (int32_t j = 0; j < W; j += U) {
-      int32_t c[U];
-      float m[U][kIPT];
-      float4 xv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const bool ok = j + u < W;
-        const int64_t p = base + C * (j + u) + r;
-        if constexpr (KIND == kStates) {
-          const int2 e = ok ? __ldg(a.Lcw + p) : make_int2(rr, 0);
-          const int f = ok ? (int)__ldg(a.Lfc + p) : 0;
-          c[u] = e.x;
-          const float w = __int_as_float(e.y);
-#pragma unroll
-          for (int jj = 0; jj < kIPT; ++jj) m[u][jj] = f > st[jj] ? w : 0.0f;
-        } else {
-          c[u] = ok ? __ldg(a.Lcol + p) : rr;
-          const float4 w4 = ok ? __ldg(reinterpret_cast<const float4*>(a.Lw + p * a.BS) + q)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-          m[u][0] = w4.x; m[u][1] = w4.y; m[u][2] = w4.z; m[u][3] = w4.w;
-        }
-      }
+    LEnt<KIND> en[PIPE ? U : 1];
+    if constexpr (PIPE) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        xv[u] = j + u < W ? X[(int64_t)c[u] * TPR + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        en[u] = l_load<KIND>(a, base + C * (j + U + u) + r, j + U + u < W, rr, q);
+    }
+    if constexpr (SMEM) gather_wait();
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+    for (int u = 0; u < U; ++u) {
+      if (j + u < W) {
+        float4 x;
+        if constexpr (SMEM) x = slots[u * kBBlock];
+        else x = xv[u];
 #pragma unroll
         for (int jj = 0; jj < kIPT; ++jj) {
-          dsum[jj] += m[u][jj];
-          acc[jj] = fmaf(m[u][jj], get4(xv[u], jj), acc[jj]);
+          const float m = l_weight<KIND>(e[u], jj, st);
+          if constexpr (KIND != kSets) dsum[jj] += m;
+          acc[jj] = fmaf(m, get4(x, jj), acc[jj]);
         }
+      }
     }
-    float4 y;
+    if constexpr (PIPE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) e[u] = en[u];
+    }
+  }
+  float4 y;
+  if constexpr (KIND == kSets) {
+    // CSR form: L_ii x_i + sum of (-w) x_c over free columns
+    const float d = a.d32[rr];
+#pragma unroll
+    for (int jj = 0; jj < kIPT; ++jj) set4(y, jj, fmaf(d, get4(xi, jj), acc[jj]));
+  } else {
+    // edge form: sum of m (x_i - x_c); an identity row where all m are 0
 #pragma unroll
     for (int jj = 0; jj < kIPT; ++jj)
       set4(y, jj, dsum[jj] == 0.0f ? get4(xi, jj) : fmaf(dsum[jj], get4(xi, jj), -acc[jj]));
-    return y;
   }
+  return y;
 }
 
 // (L_b x)_i in FP64 (the residual of a reliable update)
@@ -307,48 +376,77 @@ __device__ __forceinline__ void l_row64(const BatchArgs& a, int64_t s, int r, in
 }
 
 // One FSAI half (h = 0: G, h = 1: G^T) for the four instances of lane (r, q)
-template <int U>
-__device__ __forceinline__ float4 g_row(const BatchArgs& a, int h, int64_t s, int r, int q,
-                                        int32_t row, const float4* __restrict__ X) {
+struct GEnt {
+  int32_t c;
+  uint2 g;       // four BF16 values (per-instance factors) or one, repeated
+};
+__device__ __forceinline__ GEnt g_load(const BatchArgs& a, int h, int64_t p, bool ok,
+                                       int32_t rr, int q) {
+  GEnt e;
+  e.c = ok ? __ldg(a.Gcol[h] + p) : rr;
+  if (!ok) {
+    e.g = make_uint2(0u, 0u);
+  } else if (a.Gb[h]) {
+    e.g = __ldg(reinterpret_cast<const uint2*>(a.Gb[h] + p * a.BS) + q);
+  } else {
+    const unsigned bits = __bfloat16_as_ushort(a.Gv[h][p]);
+    e.g = make_uint2(bits | (bits << 16), bits | (bits << 16));
+  }
+  return e;
+}
+
+template <int U, bool SMEM, bool PIPE>
+__device__ __forceinline__ float4 g_row(const BatchArgs& a, int h, int32_t base, int32_t W,
+                                        int r, int q, int32_t row,
+                                        const float4* __restrict__ X) {
   const int C = a.C, TPR = a.TPR;
-  const int32_t base = a.Gsptr[h][s];
-  const int32_t W = (a.Gsptr[h][s + 1] - base) / C;
   const int32_t rr = row >= 0 ? row : 0;
-  const int32_t* __restrict__ col = a.Gcol[h];
-  const __nv_bfloat16* __restrict__ gv = a.Gv[h];
-  const __nv_bfloat16* __restrict__ gb = a.Gb[h];
+  float4* slots = gather_slots();
   float acc[kIPT] = {0.f, 0.f, 0.f, 0.f};
+  GEnt e[U];
+  if constexpr (PIPE) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) e[u] = g_load(a, h, base + C * u + r, u < W, rr, q);
+  }
   for (int32_t j = 0; j < W; j += U) {
-    int32_t c[U];
-    float g[U][kIPT];
-    float4 xv[U];
+    if constexpr (!PIPE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) e[u] = g_load(a, h, base + C * (j + u) + r, j + u < W, rr, q);
+    }
+    float4 xv[SMEM ? 1 : U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const bool ok = j + u < W;
-      const int64_t p = base + C * (j + u) + r;
-      c[u] = ok ? __ldg(col + p) : rr;
-      if (!ok) {
-#pragma unroll
-        for (int jj = 0; jj < kIPT; ++jj) g[u][jj] = 0.0f;
-      } else if (gb) {
-        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(gb + p * a.BS) + q);
-        const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
-        const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
-        g[u][0] = __low2float(lo); g[u][1] = __high2float(lo);
-        g[u][2] = __low2float(hi); g[u][3] = __high2float(hi);
+      if constexpr (SMEM) {
+        if (j + u < W) gather_async(slots + u * kBBlock, X + (int64_t)e[u].c * TPR + q);
       } else {
-        const float gs = __bfloat162float(gv[p]);
-#pragma unroll
-        for (int jj = 0; jj < kIPT; ++jj) g[u][jj] = gs;
+        xv[u] = j + u < W ? X[(int64_t)e[u].c * TPR + q] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+    GEnt en[PIPE ? U : 1];
+    if constexpr (PIPE) {
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      xv[u] = j + u < W ? X[(int64_t)c[u] * TPR + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < U; ++u)
+        en[u] = g_load(a, h, base + C * (j + U + u) + r, j + U + u < W, rr, q);
+    }
+    if constexpr (SMEM) gather_wait();
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < U; ++u) {
+      if (j + u < W) {
+        float4 x;
+        if constexpr (SMEM) x = slots[u * kBBlock];
+        else x = xv[u];
+        const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&e[u].g.x);
+        const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&e[u].g.y);
+        acc[0] = fmaf(__low2float(lo), x.x, acc[0]);
+        acc[1] = fmaf(__high2float(lo), x.y, acc[1]);
+        acc[2] = fmaf(__low2float(hi), x.z, acc[2]);
+        acc[3] = fmaf(__high2float(hi), x.w, acc[3]);
+      }
+    }
+    if constexpr (PIPE) {
 #pragma unroll
-      for (int jj = 0; jj < kIPT; ++jj) acc[jj] = fmaf(g[u][jj], get4(xv[u], jj), acc[jj]);
+      for (int u = 0; u < U; ++u) e[u] = en[u];
+    }
   }
   return make_float4(acc[0], acc[1], acc[2], acc[3]);
 }
@@ -369,7 +467,7 @@ struct Acc2 {
 // The vector phases run in element order: element e of a [n][BS] vector
 // seen as float4s belongs to quad e % TPR, and with a stride that is a
 // multiple of 1024 every thread stays on its own quad q = lane % TPR.
-template <int KIND, int U>
+template <int KIND, int U, bool SMEM, bool PIPE>
 __global__ void __launch_bounds__(kBBlock, 1)
 pcg_batched_persistent(BatchArgs a) {
   // barrier test: bar[3] != 0 withholds the last block, so the others'
@@ -399,12 +497,98 @@ pcg_batched_persistent(BatchArgs a) {
   auto any4 = [&](const int* flags) {
     return flags[kIPT * q] | flags[kIPT * q + 1] | flags[kIPT * q + 2] | flags[kIPT * q + 3];
   };
-  // the slices of this block: one per warp in each window it owns
+  // the slices of this block: one per warp in each window it owns.  Slices
+  // are sorted by length inside a window, so the warp-to-slice assignment
+  // rotates by 13 (coprime to 32) from window to window: every warp gets
+  // long and short slices alike instead of warp 0 always the longest.
   auto windows = [&](const int32_t* perm, auto&& body) {
-    for (int64_t win = blockIdx.x; win < a.nwin; win += gridDim.x) {
-      const int64_t s = win * kBWarps + warp;
+    int k = 0;
+    for (int64_t win = blockIdx.x; win < a.nwin; win += gridDim.x, ++k) {
+      const int64_t s = win * kBWarps + ((warp + 13 * k) & (kBWarps - 1));
       body(s, __ldg(perm + s * C + r));
     }
+  };
+  // The same, with lane 0 of each warp first prefetching into L2 what its
+  // next slice (the block's next window) will read: the slice's structure
+  // (pf_struct(s_next)) and a 1/32 share of the window's rows of the
+  // vectors V0, V1 (gathered or read by row).  The prefetches run ahead on
+  // the copy engine while the warp works on the current slice.
+  const int64_t vq_win = (int64_t)kBWarps * C * TPR;             // float4 per window
+  auto pf_rows = [&](const float4* V, int64_t nxt) {
+    const int64_t share = vq_win / kBWarps;
+    l2_prefetch(V + nxt * vq_win + warp * share, sizeof(float4) * share, V, V + n * TPR);
+  };
+  auto windows_pf = [&](const int32_t* perm, const int32_t* sptr, auto&& pf_struct,
+                        const float4* V0, const float4* V1, auto&& body) {
+    int64_t win = blockIdx.x;
+    if (win >= a.nwin) return;
+    int k = 0;
+    auto slice_of = [&](int64_t w, int kk) {
+      return w * kBWarps + ((warp + 13 * kk) & (kBWarps - 1));
+    };
+    int64_t s = slice_of(win, 0);
+    int32_t row = __ldg(perm + s * C + r), b0 = __ldg(sptr + s), b1 = __ldg(sptr + s + 1);
+    for (;;) {
+      // the next window's slice indices are loaded now, so their latency
+      // overlaps this window's work instead of starting the next one
+      const int64_t nxt = win + gridDim.x;
+      int64_t s2 = 0;
+      int32_t row2 = -1, c0 = 0, c1 = 0;
+      if (nxt < a.nwin) {
+        s2 = slice_of(nxt, k + 1);
+        row2 = __ldg(perm + s2 * C + r);
+        c0 = __ldg(sptr + s2);
+        c1 = __ldg(sptr + s2 + 1);
+        if (lane == 0) {
+          pf_struct(s2);
+          if (V0) pf_rows(V0, nxt);
+          if (V1) pf_rows(V1, nxt);
+        }
+      }
+      body(b0, (b1 - b0) / C, row);
+      if (nxt >= a.nwin) break;
+      win = nxt;
+      ++k;
+      s = s2;
+      row = row2;
+      b0 = c0;
+      b1 = c1;
+    }
+  };
+  auto pf_L = [&](int64_t sn) {
+    const int64_t b0 = a.Lsptr[sn], b1 = a.Lsptr[sn + 1];
+    if constexpr (KIND == kFields) {
+      l2_prefetch(a.Lcol + b0, 4 * (b1 - b0), a.Lcol, a.Lcol + a.Ltotal);
+      l2_prefetch(a.Lw + b0 * BS, 4 * BS * (b1 - b0), a.Lw, a.Lw + a.Ltotal * BS);
+    } else {
+      l2_prefetch(a.Lcw + b0, 8 * (b1 - b0), a.Lcw, a.Lcw + a.Ltotal);
+      if constexpr (KIND == kStates) l2_prefetch(a.Lfc + b0, b1 - b0, a.Lfc, a.Lfc + a.Ltotal);
+    }
+  };
+  auto pf_G = [&](int h, int64_t sn) {
+    const int64_t b0 = a.Gsptr[h][sn], b1 = a.Gsptr[h][sn + 1];
+    l2_prefetch(a.Gcol[h] + b0, 4 * (b1 - b0), a.Gcol[h], a.Gcol[h] + a.Gtotal[h]);
+    if (a.Gb[h])
+      l2_prefetch(a.Gb[h] + b0 * BS, 2 * BS * (b1 - b0), a.Gb[h], a.Gb[h] + a.Gtotal[h] * BS);
+    else
+      l2_prefetch(a.Gv[h] + b0, 2 * (b1 - b0), a.Gv[h], a.Gv[h] + a.Gtotal[h]);
+  };
+  // device time of the phases of the FP32 iterations, taken by thread 0 of
+  // block 0 as it leaves each grid barrier (every block leaves a barrier at
+  // about the same time): SpMM, x/r update, FSAI lower half, upper half,
+  // p update
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  __shared__ unsigned long long t_last;
+  __shared__ double ph[6];                 // [5]: iterations timed
+  if (timer) {
+    t_last = 0;
+    for (int k = 0; k < 6; ++k) ph[k] = 0.0;
+  }
+  auto mark = [&](int k) {
+    if (!timer) return;
+    const unsigned long long t = global_ns();
+    if (k >= 0) ph[k] += (double)(t - t_last);
+    t_last = t;
   };
   auto vec4 = [&](const float* v) {
     float4 o;
@@ -472,17 +656,20 @@ pcg_batched_persistent(BatchArgs a) {
   __syncthreads();
 
   // z = M r = G^T (G r) on the instances in `flags`, with r.z per instance
-  auto apply_precond = [&](const int* flags) -> bool {
+  auto apply_precond = [&](const int* flags, bool timed) -> bool {
     if (any4(flags))
-      windows(a.Gperm[0], [&](int64_t s, int32_t row) {
-        const float4 y = g_row<U>(a, 0, s, r, q, row, R);
+      windows_pf(a.Gperm[0], a.Gsptr[0], [&](int64_t sn) { pf_G(0, sn); }, R, nullptr,
+                 [&](int32_t base, int32_t W, int32_t row) {
+        const float4 y = g_row<U, SMEM, PIPE>(a, 0, base, W, r, q, row, R);
         if (row >= 0) T[(int64_t)row * TPR + q] = y;
       });
     if (!bgrid_sync(a.bar, err)) return false;
+    if (timed) mark(2);
     Acc2 acc[kIPT];
     if (any4(flags))
-      windows(a.Gperm[1], [&](int64_t s, int32_t row) {
-        const float4 zi = g_row<U>(a, 1, s, r, q, row, T);
+      windows_pf(a.Gperm[1], a.Gsptr[1], [&](int64_t sn) { pf_G(1, sn); }, T, R,
+                 [&](int32_t base, int32_t W, int32_t row) {
+        const float4 zi = g_row<U, SMEM, PIPE>(a, 1, base, W, r, q, row, T);
         if (row < 0) return;
         Z[(int64_t)row * TPR + q] = zi;
         const float4 ri = R[(int64_t)row * TPR + q];
@@ -492,12 +679,14 @@ pcg_batched_persistent(BatchArgs a) {
     double v[kIPT];
 #pragma unroll
     for (int j = 0; j < kIPT; ++j) v[j] = acc[j].get();
-    return breduce(v, a, parity, S, shw, err);
+    if (!breduce(v, a, parity, S, shw, err)) return false;
+    if (timed) mark(3);
+    return true;
   };
 
   for (;;) {
     // ---- segment start for the active instances: z = M r, p = z + beta p
-    if (!apply_precond(S.active)) return;
+    if (!apply_precond(S.active, false)) return;
     if (threadIdx.x < BS) {
       const int i = threadIdx.x;
       const double rzn = S.red[i];
@@ -515,14 +704,16 @@ pcg_batched_persistent(BatchArgs a) {
       }
     }
     if (!bgrid_sync(a.bar, err)) return;
+    mark(-1);
 
     // ---- FP32 iterations until every working instance is frozen
     for (;;) {
       {
         Acc2 acc[kIPT];
         if (any4(S.iterating))
-          windows(a.Lperm, [&](int64_t s, int32_t row) {
-            const float4 qi = l_row<KIND, U>(a, s, r, q, row, st, Pv);
+          windows_pf(a.Lperm, a.Lsptr, pf_L, Pv, nullptr,
+                     [&](int32_t base, int32_t W, int32_t row) {
+            const float4 qi = l_row<KIND, U, SMEM, PIPE>(a, base, W, r, q, row, st, Pv);
             if (row < 0) return;
             Q[(int64_t)row * TPR + q] = qi;
             const float4 pi = Pv[(int64_t)row * TPR + q];
@@ -533,6 +724,7 @@ pcg_batched_persistent(BatchArgs a) {
 #pragma unroll
         for (int j = 0; j < kIPT; ++j) v[j] = acc[j].get();
         if (!breduce(v, a, parity, S, shw, err)) return;
+        mark(0);
       }
       if (threadIdx.x < BS) {
         const int i = threadIdx.x;
@@ -563,6 +755,7 @@ pcg_batched_persistent(BatchArgs a) {
 #pragma unroll
         for (int j = 0; j < kIPT; ++j) v[j] = acc[j].get();
         if (!breduce(v, a, parity, S, shw, err)) return;
+        mark(1);
       }
       if (threadIdx.x < BS) {
         const int i = threadIdx.x;
@@ -572,6 +765,7 @@ pcg_batched_persistent(BatchArgs a) {
           if (rr <= S.tol2[i] || S.iters[i] >= a.max_iter || !isfinite(rr)) S.iterating[i] = 0;
         }
       }
+      __syncthreads();   // instances 32..63 are updated by warp 1: count after both
       if (threadIdx.x == 0) {
         int c = 0;
         for (int i = 0; i < BS; ++i) c += S.iterating[i];
@@ -580,7 +774,7 @@ pcg_batched_persistent(BatchArgs a) {
       __syncthreads();
       if (S.count == 0) break;
       // preconditioner on the iterating instances
-      if (!apply_precond(S.iterating)) return;
+      if (!apply_precond(S.iterating, true)) return;
       if (threadIdx.x < BS) {
         const int i = threadIdx.x;
         if (S.iterating[i]) {
@@ -605,7 +799,10 @@ pcg_batched_persistent(BatchArgs a) {
         }
       }
       if (!bgrid_sync(a.bar, err)) return;
+      mark(4);
+      if (timer) ph[5] += 1.0;
     }
+    mark(-1);
 
     // ---- reliable update of the active instances
     if (any4(S.active))
@@ -651,6 +848,7 @@ pcg_batched_persistent(BatchArgs a) {
         }
       }
     }
+    __syncthreads();   // as above: every instance updated before the count
     if (threadIdx.x == 0) {
       int c = 0;
       for (int i = 0; i < BS; ++i) c += S.active[i];
@@ -662,6 +860,10 @@ pcg_batched_persistent(BatchArgs a) {
   if (blockIdx.x == 0 && threadIdx.x < BS) {
     a.iters[threadIdx.x] = S.iters[threadIdx.x];
     a.result[BS + threadIdx.x] = S.bnorm2[threadIdx.x];
+  }
+  if (timer) {
+    for (int k = 0; k < 5; ++k) a.phase[k] = ph[k] * 1e-6;   // ms
+    a.phase[5] = ph[5];
   }
 }
 
@@ -801,9 +1003,18 @@ __device__ __forceinline__ uint64_t spread21(uint64_t v) {
   return v;
 }
 
+// Sort key of a node for the batched numbering: the box is cut into
+// 2^t x 2^t x 2^t tiles, taken in natural order (x fastest, then y, z), and
+// the nodes of a tile in Morton order of their position inside it (21 - t
+// bits per coordinate, interleaved, x lowest).  Inside a tile the order is
+// compact, so a window of consecutive nodes is a small patch; across tiles
+// it sweeps the box in slabs, so the patches worked on at the same time, and
+// their neighbours, are close together.
 __global__ void morton_keys_kernel(int64_t n, const double* __restrict__ xyz, double3 lo,
-                                   double3 scale, uint64_t* __restrict__ key,
+                                   double3 scale, int t, uint64_t* __restrict__ key,
                                    uint32_t* __restrict__ val) {
+  const int lb = 21 - t;                                 // bits inside a tile
+  const uint64_t lmask = (1ull << lb) - 1ull;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double fx = (xyz[3 * i] - lo.x) * scale.x;
@@ -812,7 +1023,10 @@ __global__ void morton_keys_kernel(int64_t n, const double* __restrict__ xyz, do
     const uint64_t ix = (uint64_t)fmin(fmax(fx, 0.0), 2097151.0);
     const uint64_t iy = (uint64_t)fmin(fmax(fy, 0.0), 2097151.0);
     const uint64_t iz = (uint64_t)fmin(fmax(fz, 0.0), 2097151.0);
-    key[i] = spread21(ix) | (spread21(iy) << 1) | (spread21(iz) << 2);
+    const uint64_t tile = (((iz >> lb) << (2 * t)) | ((iy >> lb) << t) | (ix >> lb));
+    const uint64_t in = spread21(ix & lmask) | (spread21(iy & lmask) << 1) |
+                        (spread21(iz & lmask) << 2);
+    key[i] = (tile << (3 * lb)) | in;
     val[i] = (uint32_t)i;
   }
 }
@@ -1003,7 +1217,12 @@ static unsigned grid_for_work(const dec_ctx* ctx, int64_t work) {
       1, std::min<int64_t>((work + 255) / 256, (int64_t)ctx->num_sms * 16));
 }
 
-// Morton order of the nodes (the windows of the batched layouts)
+// Node order of the batched layouts: Morton order inside tiles of about
+// kTileNodes nodes, tiles in natural order
+#ifndef DEC_TILE_NODES
+#define DEC_TILE_NODES 1024
+#endif
+constexpr int kTileNodes = DEC_TILE_NODES;
 static dec_status build_morton(dec_ctx* ctx) {
   const int64_t n = ctx->n;
   cudaStream_t s = ctx->stream;
@@ -1021,8 +1240,11 @@ static dec_status build_morton(dec_ctx* ctx) {
   DEC_TRY(ctx->key_b.ensure(n));
   DEC_TRY(ctx->val_a.ensure(n));
   DEC_TRY(ctx->val_b.ensure(n));
-  morton_keys_kernel<<<grid_for_work(ctx, n), 256, 0, s>>>(n, ctx->xyz.p, lo, sc, ctx->key_a.p,
-                                                           ctx->val_a.p);
+  // tiles of about kTileNodes nodes: 2^t per axis, t = floor(log2(cbrt(n / kTileNodes)))
+  int t = 0;
+  while (t < 10 && (double)(1 << (3 * (t + 1))) * kTileNodes <= (double)n) ++t;
+  morton_keys_kernel<<<grid_for_work(ctx, n), 256, 0, s>>>(n, ctx->xyz.p, lo, sc, t,
+                                                           ctx->key_a.p, ctx->val_a.p);
   DEC_TRY(cudaGetLastError());
   ctx->launches += 2;
   bool alt = false;
@@ -1150,18 +1372,23 @@ dec_status batch_refresh_values(dec_ctx* ctx) {
   return batch_values(ctx);
 }
 
-// Kernel variants: entries per round trip (U) for the context's instance
-// kind.  All variants of a kind add a row's entries in the same order, so
-// the choice never changes a result.
-constexpr int kGatherVariants[] = {2, 4, 8};
-constexpr int kNumGatherVariants = 3;
+// Kernel variants for the context's instance kind: entries per round trip
+// (U), whether the next round's structure loads overlap the gathers, and
+// where the gathers go (registers or shared memory); reported as
+// 100 * shared + 10 * overlapped + U.  All variants of a kind add a row's
+// entries in the same order, so the choice never changes a result.
+constexpr int kNumGatherVariants = 5;
+constexpr int kGatherVariants[kNumGatherVariants] = {2, 4, 12, 114, 106};
+constexpr int kGatherSmem[kNumGatherVariants] = {0, 0, 0, gather_smem<4>(), gather_smem<6>()};
 
 template <int KIND>
 static const void* batch_kernel(int v) {
   switch (v) {
-    case 0: return (const void*)pcg_batched_persistent<KIND, 2>;
-    case 1: return (const void*)pcg_batched_persistent<KIND, 4>;
-    default: return (const void*)pcg_batched_persistent<KIND, 8>;
+    case 0: return (const void*)pcg_batched_persistent<KIND, 2, false, false>;
+    case 1: return (const void*)pcg_batched_persistent<KIND, 4, false, false>;
+    case 2: return (const void*)pcg_batched_persistent<KIND, 2, false, true>;
+    case 3: return (const void*)pcg_batched_persistent<KIND, 4, true, true>;
+    default: return (const void*)pcg_batched_persistent<KIND, 6, true, false>;
   }
 }
 
@@ -1185,7 +1412,10 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   bool any = false;
   for (int v = 0; v < kNumGatherVariants; ++v) {
     int per_sm = 0;
-    DEC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[v], kBBlock, 0));
+    DEC_TRY(cudaFuncSetAttribute(kern[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kGatherSmem[v]));
+    DEC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[v], kBBlock,
+                                                          kGatherSmem[v]));
     usable[v] = per_sm >= 1;
     any = any || usable[v];
   }
@@ -1201,13 +1431,18 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   int* status = reinterpret_cast<int*>(ctx->coop.p + 2);
   int* its = reinterpret_cast<int*>(ctx->coop.p + 16);
   double* result = reinterpret_cast<double*>(ctx->coop.p + 16 + kBMax / 2);
+  double* phase = reinterpret_cast<double*>(ctx->coop.p + 16 + kBMax / 2 + 2 * kBMax);
   BatchArgs a{};
+  a.phase = phase;
   a.n = n;
   a.B = B;
   a.BS = BS;
   a.TPR = BS / kIPT;
   a.C = 32 / a.TPR;
   a.nwin = (n + ctx->bL.R - 1) / ctx->bL.R;
+  a.Ltotal = ctx->bL.total;
+  a.Gtotal[0] = ctx->bGlo.total;
+  a.Gtotal[1] = ctx->bGup.total;
   a.Lperm = ctx->bL.perm.p;
   a.Lsptr = ctx->bL.sptr.p;
   a.Lcw = ctx->bLcw.p;
@@ -1247,7 +1482,8 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
     cudaError_t e = cudaMemsetAsync(ctx->coop.p, 0, sizeof(int64_t) * (16 + 3 * kBMax), s);
     if (e == cudaSuccess) e = write_barrier_test(ctx, bar);
     if (e == cudaSuccess)
-      e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args, 0, s);
+      e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args,
+                                      kGatherSmem[v], s);
     ctx->launches += 1;
     return e;
   };
@@ -1307,7 +1543,8 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
     cudaError_t e = cudaMemsetAsync(ctx->coop.p, 0, sizeof(int64_t) * (16 + 3 * kBMax), s);
     if (e == cudaSuccess) e = write_barrier_test(ctx, bar);
     if (e == cudaSuccess)
-      e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args, 0, s);
+      e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args,
+                                      kGatherSmem[v], s);
     ctx->launches += 1;
     DEC_TRY(e);
   }
@@ -1321,6 +1558,8 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   DEC_TRY(cudaMemcpyAsync(hs, status, sizeof(hs), cudaMemcpyDeviceToHost, s));
   DEC_TRY(cudaMemcpyAsync(hi, its, sizeof(int) * BS, cudaMemcpyDeviceToHost, s));
   DEC_TRY(cudaMemcpyAsync(hr, result, sizeof(double) * 2 * BS, cudaMemcpyDeviceToHost, s));
+  DEC_TRY(cudaMemcpyAsync(ctx->batch_phase_ms, phase, sizeof(double) * 6,
+                          cudaMemcpyDeviceToHost, s));
   DEC_TRY(cudaStreamSynchronize(s));
   float kms = 0.0f;
   DEC_TRY(cudaEventElapsedTime(&kms, k0, k1));

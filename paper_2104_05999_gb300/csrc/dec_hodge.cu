@@ -201,11 +201,27 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
       // sub-triangles (6 edge midpoints, 4 face circumcentres, c_T) are
       // computed once per disc; a sub-triangle strictly on one side of the
       // plane cannot be cut and skips the exact test.
+      const float RTf = (float)RT;
       auto test_disc = [&](int id) {
         const double* dsc = grid.discs + 7 * (int64_t)id;
         V3 dc = mk(dsc[0], dsc[1], dsc[2]);
         V3 dn = mk(dsc[3], dsc[4], dsc[5]);
         const double r = dsc[6];
+        {
+          // FP32 pre-test of the two FP64 rejections below, on the FP64
+          // offset v = c_T - centre rounded to FP32: it rejects only where
+          // its error bound (relative to |v|, so scale-free) keeps it on the
+          // same side as the FP64 test, and the FP64 test decides the rest
+          const V3 v = cTa - dc;
+          const float vx = (float)v.x, vy = (float)v.y, vz = (float)v.z;
+          const float nx = (float)dn.x, ny = (float)dn.y, nz = (float)dn.z;
+          const float vv = vx * vx + vy * vy + vz * vz;
+          const float dpf = vx * nx + vy * ny + vz * nz;
+          const float vabs = sqrtf(vv);
+          if (fabsf(dpf) > RTf * 1.000001f + 1e-6f * vabs) return;   // ball misses the plane
+          const float reachf = (float)(grid.smax * r) * 1.000001f + RTf * 1.000001f;
+          if (vv - dpf * dpf > reachf * reachf + 1e-5f * vv) return;   // misses the disc
+        }
         {
           const V3 v = cTa - dc;
           const double dp = dot(v, dn);

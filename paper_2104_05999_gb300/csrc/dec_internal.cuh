@@ -175,6 +175,7 @@ struct dec_ctx {
   int64_t batch_tune_key[4][2] = {};       // (n, nnz) each choice was tuned for
   int batch_variant_used = -1;             // variant of the last batched solve
   double batch_kernel_ms = -1.0;           // device time of its persistent launch
+  double batch_phase_ms[6] = {};           // its per-phase times and FP32 iterations
   int64_t crack_iters = 0;                 // CG iterations of the last crack growth
   bool batch_per_instance = false;         // per-instance FSAI factors
   dec::DevBuf<float> bx, br, bz, bp, bq, bt;
