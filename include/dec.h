@@ -311,6 +311,55 @@ dec_status dec_crack_paths(dec_ctx* ctx, int32_t n_paths, int32_t max_steps,
                            const int32_t* orders, double rtol, int32_t max_iter,
                            double k_stop, double* k_eff, int32_t* steps);
 
+/* ---- the paper's own tet-centred form ---- */
+
+/* Solve the mixed system of Sec. 2.3 (Eq. 11-13) with one potential per tet
+ * and one flux per triangular face, the flux block eliminated as the
+ * paper's Schur-complement solve does: the flux block (1/kappa) *2 is
+ * diagonal (*2_f = signed circumcentric dual edge length / face area), so
+ * the potentials alpha solve the two-point operator
+ *   sum over the faces f of T of w_f (alpha_T - alpha_T'),  w_f = kappa / *2_f,
+ * where a face whose three nodes are Dirichlet ties alpha_T to the mean T0
+ * of those nodes and any other boundary face carries the prescribed outward
+ * flux (Eq. 13; none: zero flux).  Sec. 3.1's limiter raises *2 entries
+ * below `limiter` to it.  Cracked faces (Sec. 2.5) get w_f = 0.  FP64 PCG
+ * (Jacobi) from alpha = 0 to ||b - S alpha|| <= rtol ||b||.
+ *   T0            [n_nodes] f64 host or device: node values (read on
+ *                 Dirichlet nodes).
+ *   kappa         conductivity, > 0.  limiter: <= 0 for none (e.g. 1e-8).
+ *   cracked_faces [n_cracked] int32 host or device face ids
+ *                 (dec_tet_get_faces numbering), or NULL.
+ *   face_flux     [n_faces] f64 host or device outward flux through each
+ *                 face (read on non-Dirichlet boundary faces), or NULL.
+ *   alpha         [n_tets] f64 host or device, or NULL: potential per tet
+ *                 (at its circumcentre).
+ *   q2            [2] f64 host, or NULL: heat entering through the Dirichlet
+ *                 faces on x = 0 and leaving through those on x = 1.
+ *   iters, relres, n_limited   host outputs, or NULL.
+ * A tet whose faces all carry w = 0 gets alpha = 0; a group of tets cut off
+ * from every Dirichlet face keeps alpha = 0 (its block is singular with a
+ * zero right-hand side unless face fluxes enter it).  Needs an uploaded
+ * mesh only (independent of the node-form calls).  Errors: DEC_ERR_STATE,
+ * DEC_ERR_ARG (also a cracked face id out of range), DEC_ERR_BREAKDOWN,
+ * DEC_NOT_CONVERGED (outputs still written), DEC_ERR_TIMEOUT. */
+dec_status dec_tet_solve(dec_ctx* ctx, const double* T0, double kappa, double limiter,
+                         const int32_t* cracked_faces, int64_t n_cracked,
+                         const double* face_flux, double rtol, int32_t max_iter, double* alpha,
+                         double* q2, int32_t* iters, double* relres, int64_t* n_limited);
+
+/* Faces of the uploaded mesh: the sorted node triples (i < j < k) in
+ * lexicographic order, and the face opposite local vertex v of tet t at
+ * t2f[t*4 + v].  n_faces host; faces [n_faces*3] and t2f [n_tets*4] int32
+ * host or device, either may be NULL. */
+dec_status dec_tet_get_faces(dec_ctx* ctx, int64_t* n_faces, int32_t* faces, int32_t* t2f);
+
+/* Flux vector at each tet's barycentre from the last dec_tet_solve
+ * (Whitney 2-form interpolation of the face fluxes, the paper's vector
+ * output): v = sum_i phi_i (b - x_i) / (3 V), phi_i the outward flux through
+ * the face opposite vertex i.  v [n_tets*3] f64 host or device.
+ * DEC_ERR_STATE without a solution. */
+dec_status dec_tet_whitney(dec_ctx* ctx, double* v);
+
 /* CG iterations summed over the steps of the last dec_crack_evolve or
  * dec_crack_paths call (over all paths; the first solve before any crack
  * not counted). */

@@ -58,6 +58,9 @@ SIGNATURES = {
     "dec_get_batch_phase_ms": [_P, _P],
     "dec_get_crack_iterations": [_P, _P],
     "dec_crack_paths": [_P, _I32, _I32, _P, _D, _I32, _D, _P, _P],
+    "dec_tet_solve": [_P, _P, _D, _D, _P, _I64, _P, _D, _I32, _P, _P, _P, _P, _P],
+    "dec_tet_get_faces": [_P, _P, _P, _P],
+    "dec_tet_whitney": [_P, _P],
     "dec_get_sizes": [_P, _P, _P, _P, _P, _P],
     "dec_get_edges": [_P, _P, _P],
     "dec_get_hodge": [_P, _P, _P],
@@ -235,6 +238,45 @@ class Context:
         if raise_on_error:
             self._check(st)
         return st, [keff[b, :steps[b]].copy() for b in range(P)], steps
+
+    def dec_tet_solve(self, T0, kappa=1.0, limiter=1e-8, cracked_faces=None,
+                      face_flux=None, rtol=1e-12, max_iter=100000, raise_on_error=True):
+        """The paper's tet-centred form; returns dict(status, alpha, q_in,
+        q_out, iters, relres, limited)."""
+        n, m = self.sizes()[:2]
+        alpha = np.zeros(m)
+        q2 = np.zeros(2)
+        it = C.c_int32()
+        rr = C.c_double()
+        nl = C.c_int64()
+        cf = None if cracked_faces is None else np.ascontiguousarray(cracked_faces, dtype=np.int32)
+        st = self.lib.dec_tet_solve(
+            self.h, _ptr(np.ascontiguousarray(T0, dtype=np.float64), np.float64),
+            float(kappa), float(limiter), None if cf is None else cf.ctypes.data,
+            0 if cf is None else len(cf),
+            None if face_flux is None else _ptr(np.ascontiguousarray(face_flux, dtype=np.float64), np.float64),
+            float(rtol), int(max_iter), alpha.ctypes.data, q2.ctypes.data, C.byref(it),
+            C.byref(rr), C.byref(nl))
+        if raise_on_error:
+            self._check(st)
+        return dict(status=st, alpha=alpha, q_in=q2[0], q_out=q2[1], iters=it.value,
+                    relres=rr.value, limited=nl.value)
+
+    def dec_tet_get_faces(self):
+        m = self.sizes()[1]
+        nf = C.c_int64()
+        self._check(self.lib.dec_tet_get_faces(self.h, C.byref(nf), None, None))
+        faces = np.zeros((nf.value, 3), dtype=np.int32)
+        t2f = np.zeros((m, 4), dtype=np.int32)
+        self._check(self.lib.dec_tet_get_faces(self.h, C.byref(nf), faces.ctypes.data,
+                                               t2f.ctypes.data))
+        return faces, t2f
+
+    def dec_tet_whitney(self):
+        m = self.sizes()[1]
+        v = np.zeros((m, 3))
+        self._check(self.lib.dec_tet_whitney(self.h, v.ctypes.data))
+        return v
 
     # ---- getters --------------------------------------------------------
     def dec_get_batch_variant(self):

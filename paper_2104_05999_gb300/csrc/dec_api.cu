@@ -126,6 +126,8 @@ dec_status dec_mesh_upload(dec_ctx* ctx, const double* xyz, int64_t n_nodes,
   ctx->stage = 0;
   ctx->n = n_nodes;
   ctx->m = n_tets;
+  ctx->nf = 0;              // faces of the tet-centred form: rebuilt on demand
+  ctx->tet_solved = false;
   cudaStream_t s = ctx->stream;
   DEC_TRY(upload(ctx->xyz, xyz, 3 * n_nodes, s));
   DEC_TRY(upload(ctx->tets, tets, 4 * n_tets, s));
@@ -515,6 +517,72 @@ dec_status dec_crack_paths(dec_ctx* ctx, int32_t n_paths, int32_t max_steps,
   ord.release();
   if (st == DEC_OK) ctx->stage = 4;   // the paths' last solutions are current
   return st;
+}
+
+dec_status dec_tet_solve(dec_ctx* ctx, const double* T0, double kappa, double limiter,
+                         const int32_t* cracked_faces, int64_t n_cracked,
+                         const double* face_flux, double rtol, int32_t max_iter, double* alpha,
+                         double* q2, int32_t* iters, double* relres, int64_t* n_limited) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 1) return ctx->fail(DEC_ERR_STATE, "tet_solve: no mesh uploaded");
+  if (!T0 || !(kappa > 0.0) || !std::isfinite(kappa) || !std::isfinite(limiter) ||
+      n_cracked < 0 || (n_cracked > 0 && !cracked_faces))
+    return ctx->fail(DEC_ERR_ARG, "tet_solve: bad T0, kappa, limiter or cracked faces");
+  if (!(rtol > 0.0) || !std::isfinite(rtol) || max_iter < 1)
+    return ctx->fail(DEC_ERR_ARG, "tet_solve: rtol > 0 and max_iter >= 1");
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  ctx->tet_solved = false;
+  DEC_TRY_STATUS(dec::tet_faces(ctx));
+  DEC_TRY(upload(ctx->tT0, T0, ctx->n, s));
+  if (n_cracked > 0) DEC_TRY(upload(ctx->tcracked, cracked_faces, n_cracked, s));
+  if (face_flux) DEC_TRY(upload(ctx->tflux, face_flux, ctx->nf, s));
+  int it = 0;
+  double rr = 0.0;
+  int64_t nl = 0;
+  dec_status st = dec::tet_solve(ctx, ctx->tT0.p, kappa, limiter,
+                                 n_cracked > 0 ? ctx->tcracked.p : nullptr, n_cracked,
+                                 face_flux ? ctx->tflux.p : nullptr, rtol, max_iter, &it, &rr,
+                                 &nl);
+  if (st == DEC_ERR_CUDA || st == DEC_ERR_ARG || st == DEC_ERR_LIMIT) return st;
+  std::string keep = ctx->err;
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  if (n_limited) *n_limited = nl;
+  if (alpha) DEC_TRY(download(alpha, (const double*)ctx->talpha.p, ctx->m, s));
+  if (q2) DEC_TRY_STATUS(dec::tet_k_eff(ctx, q2));
+  DEC_TRY(cudaStreamSynchronize(s));
+  ctx->err = keep;
+  ctx->tet_solved = st == DEC_OK || st == DEC_NOT_CONVERGED;
+  return st;
+}
+
+dec_status dec_tet_get_faces(dec_ctx* ctx, int64_t* n_faces, int32_t* faces, int32_t* t2f) {
+  if (!ctx || !n_faces) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->stage < 1) return ctx->fail(DEC_ERR_STATE, "tet_get_faces: no mesh uploaded");
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  DEC_TRY_STATUS(dec::tet_faces(ctx));
+  *n_faces = ctx->nf;
+  if (faces) DEC_TRY(download(faces, (const int32_t*)ctx->faces.p, 3 * ctx->nf, s));
+  if (t2f) DEC_TRY(download(t2f, (const int32_t*)ctx->t2f.p, 4 * ctx->m, s));
+  DEC_TRY(cudaStreamSynchronize(s));
+  return DEC_OK;
+}
+
+dec_status dec_tet_whitney(dec_ctx* ctx, double* v) {
+  if (!ctx || !v) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (!ctx->tet_solved) return ctx->fail(DEC_ERR_STATE, "tet_whitney: no tet-centred solution");
+  DEC_TRY_STATUS(set_device(ctx));
+  cudaStream_t s = ctx->stream;
+  DEC_TRY(ctx->tr.ensure(3 * ctx->m));
+  DEC_TRY_STATUS(dec::tet_whitney(ctx, ctx->tet_flux ? ctx->tflux.p : nullptr, ctx->tr.p));
+  DEC_TRY(download(v, (const double*)ctx->tr.p, 3 * ctx->m, s));
+  DEC_TRY(cudaStreamSynchronize(s));
+  return DEC_OK;
 }
 
 dec_status dec_get_crack_iterations(const dec_ctx* ctx, int64_t* iters) {

@@ -1050,11 +1050,13 @@ __global__ void renumber_layout_kernel(int64_t slots, int64_t total,
   }
 }
 
-// bounding box of the nodes: out = (min x, min y, min z, max x, max y, max z)
-__global__ void bbox_kernel(int64_t n, const double* __restrict__ xyz, double* __restrict__ out) {
+// bounding box of the nodes: per-block (min x, min y, min z, max x, max y,
+// max z) into part[6 * block], then one block folds the partials into out
+__global__ void bbox_kernel(int64_t n, const double* __restrict__ xyz, double* __restrict__ part) {
   __shared__ double sh[6][256];
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
     for (int d = 0; d < 3; ++d) {
       lo[d] = fmin(lo[d], xyz[3 * i + d]);
       hi[d] = fmax(hi[d], xyz[3 * i + d]);
@@ -1064,10 +1066,22 @@ __global__ void bbox_kernel(int64_t n, const double* __restrict__ xyz, double* _
     sh[3 + d][threadIdx.x] = hi[d];
   }
   __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int d = 0; d < 3; ++d) {
+        sh[d][threadIdx.x] = fmin(sh[d][threadIdx.x], sh[d][threadIdx.x + h]);
+        sh[3 + d][threadIdx.x] = fmax(sh[3 + d][threadIdx.x], sh[3 + d][threadIdx.x + h]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) part[6 * (int64_t)blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void bbox_fold_kernel(int nb, const double* __restrict__ part, double* __restrict__ out) {
   if (threadIdx.x < 6) {
-    double v = sh[threadIdx.x][0];
-    for (int j = 1; j < (int)blockDim.x; ++j)
-      v = threadIdx.x < 3 ? fmin(v, sh[threadIdx.x][j]) : fmax(v, sh[threadIdx.x][j]);
+    double v = part[threadIdx.x];
+    for (int b = 1; b < nb; ++b)
+      v = threadIdx.x < 3 ? fmin(v, part[6 * b + threadIdx.x]) : fmax(v, part[6 * b + threadIdx.x]);
     out[threadIdx.x] = v;
   }
 }
@@ -1226,8 +1240,10 @@ constexpr int kTileNodes = DEC_TILE_NODES;
 static dec_status build_morton(dec_ctx* ctx) {
   const int64_t n = ctx->n;
   cudaStream_t s = ctx->stream;
-  DEC_TRY(ctx->kpartial.ensure(8));
-  bbox_kernel<<<1, 256, 0, s>>>(n, ctx->xyz.p, ctx->kpartial.p);
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ctx->num_sms * 4));
+  DEC_TRY(ctx->kpartial.ensure(6 * (size_t)nb + 8));
+  bbox_kernel<<<nb, 256, 0, s>>>(n, ctx->xyz.p, ctx->kpartial.p + 8);
+  bbox_fold_kernel<<<1, 32, 0, s>>>(nb, ctx->kpartial.p + 8, ctx->kpartial.p);
   double bb[6];
   DEC_TRY(cudaMemcpyAsync(bb, ctx->kpartial.p, sizeof(bb), cudaMemcpyDeviceToHost, s));
   DEC_TRY(cudaStreamSynchronize(s));

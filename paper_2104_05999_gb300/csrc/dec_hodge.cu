@@ -97,6 +97,7 @@ struct DiscGrid {
   const int32_t* start;   // [cells+1]
   const int32_t* items;   // disc ids
   const double* discs;    // [nd][7]
+  const float4* discs_f;  // [nd][2]: (centre, bound on |centre|), (normal, reach rounded up)
   const double* scales;   // [n_states]
   int n_states;
   int nd;
@@ -165,21 +166,20 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
       first[s] = (uint8_t)grid.n_states;
     }
     if (grid.nd > 0) {
-      // absolute points of the dual sub-triangles
+      // Every dual sub-triangle of the tet lies in its circumball (c_T is
+      // the centre; m_e and c_F are projections of c_T onto an edge line and
+      // a face plane), so a disc that misses the ball cuts none of them and
+      // the candidate discs are those binned in the cells the ball's box
+      // meets.  The radius carries a relative margin; the cut decision
+      // itself stays exact.
       const V3 cTa = X[0] + cT;
+      const double RT2 = dot(cT, cT) * (1.0 + 1e-9) + 1e-300;
+      const double RT = sqrt(RT2);
+      const double lo[3] = {cTa.x - RT, cTa.y - RT, cTa.z - RT};
+      const double hi[3] = {cTa.x + RT, cTa.y + RT, cTa.z + RT};
+      // face circumcentres: only for a tet that some disc may cut
       V3 cF[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        cF[v] = tri_circumcentre(X[(v + 1) & 3], X[(v + 2) & 3], X[(v + 3) & 3]);
-      // bounding box of the 12 dual sub-triangles of the tet
-      double lo[3], hi[3];
-      lo[0] = hi[0] = cTa.x; lo[1] = hi[1] = cTa.y; lo[2] = hi[2] = cTa.z;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        lo[0] = fmin(lo[0], fmin(cF[v].x, X[v].x)); hi[0] = fmax(hi[0], fmax(cF[v].x, X[v].x));
-        lo[1] = fmin(lo[1], fmin(cF[v].y, X[v].y)); hi[1] = fmax(hi[1], fmax(cF[v].y, X[v].y));
-        lo[2] = fmin(lo[2], fmin(cF[v].z, X[v].z)); hi[2] = fmax(hi[2], fmax(cF[v].z, X[v].z));
-      }
+      bool have_cF = false;
       int c0[3], c1[3];
       bool empty = false;
 #pragma unroll
@@ -190,38 +190,44 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
         c0[d] = (int)fmax(0.0, floor(f0));
         c1[d] = (int)fmin((double)grid.dim[d] - 1.0, floor(f1));
       }
-      // Every dual sub-triangle of the tet lies in its circumball (c_T is
-      // the centre; m_e and c_F are projections of c_T onto an edge line and
-      // a face plane), so a disc that misses the ball cuts none of them.
-      // The test is conservative (the in-plane reach is bounded by r + R_T)
-      // with a relative margin; the cut decision itself stays exact.
-      const double RT2 = dot(cT, cT) * (1.0 + 1e-9) + 1e-300;
-      const double RT = sqrt(RT2);
-      // Signed distances to the disc plane of the 11 points of the 12 dual
-      // sub-triangles (6 edge midpoints, 4 face circumcentres, c_T) are
-      // computed once per disc; a sub-triangle strictly on one side of the
-      // plane cannot be cut and skips the exact test.
-      const float RTf = (float)RT;
+      // The ball test is conservative (the in-plane reach is bounded by
+      // r + R_T).  Signed distances to the disc plane of the 11 points of
+      // the 12 dual sub-triangles (6 edge midpoints, 4 face circumcentres,
+      // c_T) are computed once per disc; a sub-triangle strictly on one side
+      // of the plane cannot be cut and skips the exact test.
+      //
+      // Most candidate discs are far from the tet, and GB300's FP64 pipe is
+      // narrow, so the two rejections are first made entirely in FP32 from
+      // c_T rounded once per tet and the discs rounded once on the host.
+      // With u = 2^-24 and S = A_t + A_d (bounds on |c_T| and |centre| per
+      // coordinate), the offset v = c_T - centre carries an error of at most
+      // 2uS per coordinate, so (first order, |normal| = 1):
+      //   |dp32 - dp| <= 6 sqrt(3) u S,   |par32 - par| <= 63 u S^2
+      // (dp the distance to the disc plane, par = |v|^2 - dp^2).  The
+      // margins below are twice these plus the roundings of the thresholds,
+      // so FP32 rejects only where the FP64 test rejects too: the decisions,
+      // and so *1 and the crack states, are unchanged.
+      constexpr float kU = 5.9604645e-8f;    // 2^-24
+      const float Cx = (float)cTa.x, Cy = (float)cTa.y, Cz = (float)cTa.z;
+      const float At = fmaxf(fabsf(Cx), fmaxf(fabsf(Cy), fabsf(Cz))) * (1.0f + 2.0f * kU);
+      const float RTf = (float)RT * (1.0f + 4.0f * kU);
       auto test_disc = [&](int id) {
+        {
+          const float4 d0 = __ldg(grid.discs_f + 2 * (int64_t)id);
+          const float4 d1 = __ldg(grid.discs_f + 2 * (int64_t)id + 1);
+          const float vx = Cx - d0.x, vy = Cy - d0.y, vz = Cz - d0.z;
+          const float S = At + d0.w;
+          const float dpf = fmaf(vx, d1.x, fmaf(vy, d1.y, vz * d1.z));
+          if (fabsf(dpf) > RTf + (24.0f * S + 8.0f * RTf) * kU) return;   // ball misses the plane
+          const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+          const float par = fmaf(-dpf, dpf, vv);
+          const float T = d1.w + RTf;
+          if (par > T * T * (1.0f + 8.0f * kU) + 128.0f * kU * S * S) return;   // misses the disc
+        }
         const double* dsc = grid.discs + 7 * (int64_t)id;
         V3 dc = mk(dsc[0], dsc[1], dsc[2]);
         V3 dn = mk(dsc[3], dsc[4], dsc[5]);
         const double r = dsc[6];
-        {
-          // FP32 pre-test of the two FP64 rejections below, on the FP64
-          // offset v = c_T - centre rounded to FP32: it rejects only where
-          // its error bound (relative to |v|, so scale-free) keeps it on the
-          // same side as the FP64 test, and the FP64 test decides the rest
-          const V3 v = cTa - dc;
-          const float vx = (float)v.x, vy = (float)v.y, vz = (float)v.z;
-          const float nx = (float)dn.x, ny = (float)dn.y, nz = (float)dn.z;
-          const float vv = vx * vx + vy * vy + vz * vz;
-          const float dpf = vx * nx + vy * ny + vz * nz;
-          const float vabs = sqrtf(vv);
-          if (fabsf(dpf) > RTf * 1.000001f + 1e-6f * vabs) return;   // ball misses the plane
-          const float reachf = (float)(grid.smax * r) * 1.000001f + RTf * 1.000001f;
-          if (vv - dpf * dpf > reachf * reachf + 1e-5f * vv) return;   // misses the disc
-        }
         {
           const V3 v = cTa - dc;
           const double dp = dot(v, dn);
@@ -229,6 +235,12 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
           const double par2 = dot(v, v) - dp * dp;
           const double reach = grid.smax * r * (1.0 + 1e-9);
           if (par2 > reach * reach + 2.0 * reach * RT + RT2) return;
+        }
+        if (!have_cF) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            cF[v] = tri_circumcentre(X[(v + 1) & 3], X[(v + 2) & 3], X[(v + 3) & 3]);
+          have_cF = true;
         }
         const double sT = dot(cTa - dc, dn);
         double sF[4];
@@ -413,6 +425,26 @@ dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k, int n_fields) {
     DEC_TRY(cudaStreamSynchronize(s));
     const double smax = hs.back();
     g.smax = smax;
+    // FP32 disc records for the pre-test: centre and a bound on its largest
+    // coordinate, normal and the reach smax * r (1 + 1e-9), bounds rounded up
+    std::vector<float> hf(8 * nd);
+    constexpr double kUp = 1.0 + 2.4e-7;     // 1 + 4 * 2^-24
+    for (int64_t i = 0; i < nd; ++i) {
+      const double* d = hd.data() + 7 * i;
+      float* f = hf.data() + 8 * i;
+      double amax = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        f[k] = (float)d[k];
+        f[4 + k] = (float)d[3 + k];
+        amax = std::max(amax, std::fabs(d[k]));
+      }
+      f[3] = (float)(amax * kUp);
+      f[7] = (float)(smax * d[6] * (1.0 + 1e-9) * kUp);
+    }
+    DEC_TRY(ctx->discs_f.ensure(8 * nd));
+    DEC_TRY(cudaMemcpyAsync(ctx->discs_f.p, hf.data(), sizeof(float) * 8 * nd,
+                            cudaMemcpyHostToDevice, s));
+    g.discs_f = reinterpret_cast<const float4*>(ctx->discs_f.p);
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, rmax = 0;
     for (int64_t i = 0; i < nd; ++i) {
       const double R = hd[7 * i + 6] * smax;

@@ -123,6 +123,7 @@ struct dec_ctx {
   dec::DevBuf<double> w;           // [ne] uncracked *1
   dec::DevBuf<uint8_t> first_cut;  // [ne]
   dec::DevBuf<double> discs;       // [nd][7]
+  dec::DevBuf<float> discs_f;      // [nd][8]: FP32 copy for the crack pre-test
   dec::DevBuf<double> scales;      // [n_scales]
   dec::DevBuf<int32_t> grid_start, grid_items;
   dec::DevBuf<double> kcond;       // [m]
@@ -182,6 +183,14 @@ struct dec_ctx {
   // conductivity fields (dec_hodge_assemble_fields): instances with their
   // own *1; w then holds [n_fields][ne]
   int n_fields = 1;
+  // the tet-centred form (dec_tet_solve): faces, face data, the tet system
+  int64_t nf = 0;                          // faces of the mesh (0: not built)
+  bool tet_solved = false;
+  bool tet_flux = false;                   // the last solve had face fluxes
+  dec::DevBuf<int32_t> faces, fslot0, fslot1, t2f;
+  dec::DevBuf<double> tet_h, fw, fT0, tval, trhs, tdinv, talpha, tr, tp, tq, tT0, tflux;
+  dec::DevBuf<uint8_t> fcls, fcut;
+  dec::DevBuf<int32_t> tcol, tcracked;
   std::vector<int> iters_host;
   std::vector<double> relres_host;
 
@@ -190,7 +199,7 @@ struct dec_ctx {
     seg_pay.release(); seg_start.release(); key_a.release(); key_b.release();
     val_a.release(); val_b.release(); hist.release(); scan_tmp.release();
     flags.release(); errflag.release(); piece.release(); slot_cut.release();
-    w.release(); first_cut.release(); discs.release(); scales.release();
+    w.release(); first_cut.release(); discs.release(); discs_f.release(); scales.release();
     grid_start.release(); grid_items.release(); kcond.release(); rowptr.release();
     col.release(); eid.release(); dpos.release(); up_begin.release();
     lo_begin.release(); pos_up.release(); lo_col.release(); lo_eid.release();
@@ -209,6 +218,10 @@ struct dec_ctx {
     bb.release(); bx64.release(); br64.release(); bpartial.release();
     kpartial.release(); crack_buf.release(); bx.release(); br.release(); bz.release();
     bp.release(); bq.release(); bt.release();
+    faces.release(); fslot0.release(); fslot1.release(); t2f.release(); tet_h.release();
+    fw.release(); fT0.release(); tval.release(); trhs.release(); tdinv.release();
+    talpha.release(); tr.release(); tp.release(); tq.release(); tT0.release(); tflux.release();
+    fcls.release(); fcut.release(); tcol.release(); tcracked.release();
   }
 
   dec_status fail(dec_status s, const std::string& what) {
@@ -398,6 +411,14 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
 // shared-memory limits of the staged SELL kernels (current device)
 cudaError_t init_kernel_attributes();
 // crack growth
+// the tet-centred form
+dec_status tet_faces(dec_ctx* ctx);
+dec_status tet_solve(dec_ctx* ctx, const double* T0_dev, double kappa, double limiter,
+                     const int32_t* cracked_dev, int64_t n_cracked, const double* flux_dev,
+                     double rtol, int max_iter, int* iters, double* relres,
+                     int64_t* n_limited);
+dec_status tet_k_eff(dec_ctx* ctx, double* q2);
+dec_status tet_whitney(dec_ctx* ctx, const double* flux_dev, double* v_dev);
 dec_status crack_paths(dec_ctx* ctx, int P, int max_steps, const int32_t* orders_dev,
                        double rtol, int max_iter, double k_stop, double* k_eff,
                        int32_t* steps);
