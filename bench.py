@@ -310,6 +310,28 @@ def gpu_arm(args, rank, world):
         ("mesh_upload", "hodge_assemble", "laplacian_build", "solve", "k_eff"))}
     _log(f"phases ms: {phases}")
 
+    # the same step with FP32 geometry for well-shaped tets (DEC_GEOM_MIXED):
+    # Hodge time, tets kept in FP64 and the change of k_eff (untimed step)
+    ev2 = [_t.cuda.Event(enable_timing=True) for _ in range(2)]
+    ctx.dec_set_geom_precision(abi.DEC_GEOM_MIXED)
+    ctx.dec_mesh_upload(d_xyz, d_tets, d_tags)
+    with _t.cuda.stream(stream):
+        flush.fill_(1)
+        ev2[0].record(stream)
+    ctx.dec_hodge_assemble(d_k, d_discs, d_scales)
+    ev2[1].record(stream)
+    ev2[1].synchronize()
+    n_fp64_tets = ctx.dec_get_geom_fp64_tets()
+    ctx.dec_laplacian_build(d_T0, pc)
+    ctx.dec_solve(rtol, MAX_ITER, mode64, None)
+    q_geo = ctx.dec_k_eff()[0]
+    ctx.dec_set_geom_precision(abi.DEC_GEOM_FP64)
+    geom_mixed = {"hodge_assemble_ms": round(ev2[0].elapsed_time(ev2[1]), 4),
+                  "hodge_assemble_ms_fp64_geometry": phases["hodge_assemble"],
+                  "fp64_tets": int(n_fp64_tets), "tets": int(wl.m),
+                  "k_eff_rel_diff": float(np.max(np.abs(q_geo - q_in)) / np.max(np.abs(q_in)))}
+    _log(f"FP32 geometry: {geom_mixed}")
+
     # solve-only timing: time dec_solve alone (assembly already done)
     step(mode64)
     s_times = []
@@ -366,17 +388,13 @@ def gpu_arm(args, rank, world):
         roof_kernel = ("pcg_batched_persistent (one launch = the whole solve of "
                        "%d instances; mean of the timed steps' launches)" % B)
     roof_gbs = roof_bytes / (roof_ms * 1e-3) / 1e9
+    # DRAM traffic of the dominant kernel from an ncu capture stored in
+    # profiles/traffic.json, scaled to this launch by the units it processes;
+    # null when the kernel's source file has changed since the capture
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "spmv_f64_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            with open(tpath) as f:
-                tj = json.load(f)
-            if (tj.get("workload") == wl.name and tj.get("kernel_rev") == KERNEL_REV
-                    and want == "fp64"):
-                traffic = tj["bytes_per_launch"]
-        except Exception:
-            traffic = None
+    if want == "batched":
+        traffic = stored_traffic("pcg_batched_persistent",
+                                 n * int(np.max(iters)), B)
     clocks = clk.summary()
     # k_eff of every rank's instances, in global order
     q_all = gather_instances(q_in, world, dev)
@@ -424,6 +442,7 @@ def gpu_arm(args, rank, world):
         "e2e": {"value": round(statistics.mean(e_times), 4), "unit": "ms",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(round(launches)),
+        "geom_mixed": geom_mixed,
         "batch_variant": ctx.dec_get_batch_variant() if want == "batched" else None,
         "batch_phase_ms": ([round(float(x), 4) for x in ctx.dec_get_batch_phase_ms()]
                            if want == "batched" else None),
@@ -433,7 +452,22 @@ def gpu_arm(args, rank, world):
     return out
 
 
-KERNEL_REV = "r2"
+def stored_traffic(kernel, units, instances):
+    """Bytes per launch from profiles/traffic.json: the measured DRAM bytes
+    per unit times ``units``, if the entry was taken with ``instances``
+    instances and the SHA-256 of its source file still matches."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            entry = json.load(f)[kernel]
+        with open(os.path.join(ROOT, entry["source"]), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None
+    if digest != entry["sha256"] or entry["instances"] != instances:
+        return None
+    return int(entry["bytes_per_unit"] * units)
 
 
 def crack_growth_measure(max_steps=600, oracle_steps=3, paths=64, path_steps=200):

@@ -168,6 +168,30 @@ dec_status dec_hodge_assemble(dec_ctx* ctx, const double* k,
 dec_status dec_hodge_assemble_fields(dec_ctx* ctx, const double* k, int32_t n_fields,
                                      const double* discs, int64_t n_discs);
 
+/* geometry precisions (dec_set_geom_precision) */
+enum {
+  DEC_GEOM_FP64 = 0,    /* every tet's geometry in FP64 (the default)          */
+  DEC_GEOM_MIXED = 1    /* FP32 for well-shaped tets, FP64 for the others      */
+};
+
+/* Choose the arithmetic of the per-tet geometry (Sec. 2.1: circumcentres and
+ * the dual-face pieces over edge lengths) for the following
+ * dec_hodge_assemble and dec_hodge_assemble_fields calls of the context.
+ * DEC_GEOM_MIXED computes a tet in FP32 when L^3 <= 16 |6 V| (L its longest
+ * edge from its first vertex, V its volume; a regular tet has
+ * L^3 / |6 V| = 2.8, a Kuhn tet 5.2), in FP64 otherwise.  Crack decisions
+ * are those of the FP64 geometry: the FP32 circumcentre only serves as a
+ * filter with an error bound, and any tet that a disc may cut has its
+ * circumcentre formed again in FP64 for the exact test.  The FP32 pieces
+ * carry relative errors of order 1e-6, so *1, T and k_eff move by about
+ * that much against the FP64 geometry (DEC_GEOM_FP64 keeps agreement with
+ * the FP64 definition to 1e-12).  dec_get_geom_fp64_tets gives the number
+ * of tets the last assembly computed in FP64 (all of them with
+ * DEC_GEOM_FP64).
+ * Errors: DEC_ERR_ARG (NULL context or pointer, unknown precision). */
+dec_status dec_set_geom_precision(dec_ctx* ctx, int32_t precision);
+dec_status dec_get_geom_fp64_tets(const dec_ctx* ctx, int64_t* n_tets);
+
 /* Build the node Laplacian and the right-hand sides (Sec. 2.3, Eq. 11-13),
  * node form: L_ij = -*1_ij, L_ii = sum_j *1_ij; Dirichlet columns move to
  * the right-hand side (b_i = sum_{j in D} *1_ij T0_j), Dirichlet rows
@@ -216,13 +240,24 @@ dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy);
  * (nodes, matrix entries) at each instance stride (8, 16, 32, 64) times a
  * few iterations of every variant and keeps the fastest for the context's
  * later solves of that size.
- *   gather_entries  host: 100 * (gathers into shared memory by cp.async)
- *                   + 10 * (next entries' structure loaded while the
- *                   gathers are in flight) + matrix entries per round trip:
- *                   one of 2, 4, 12, 114, 106.
+ *   gather_entries  host: 1000 * K / 8 (K = matrix entries per chunk of a
+ *                   warp's structure staged in shared memory; Dirichlet
+ *                   sets of 8 or 16 instances only) + 100 * (gathers into
+ *                   shared memory by cp.async) + 10 * (next entries'
+ *                   structure loaded while the gathers are in flight) +
+ *                   gathers per round trip: one of 2, 4, 12, 114, 106,
+ *                   1004, 2004, 2002.
  * All variants give bit-identical results.  DEC_ERR_STATE before the first
  * batched solve.  (No counterpart in the paper: a launch-shape choice.) */
 dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries);
+
+/* Make the following batched solves of the context use one variant (a code
+ * of dec_get_batch_variant) instead of the autotuner's choice; 0 returns to
+ * the autotuner.  A solve whose batch the variant does not fit (a staged
+ * variant with crack states or fields, or more than 16 instances) fails
+ * with DEC_ERR_ARG.  Errors: DEC_ERR_ARG for an unknown code.  (No
+ * counterpart in the paper: used to compare launch shapes.) */
+dec_status dec_set_batch_variant(dec_ctx* ctx, int32_t variant);
 
 /* Device time in ms of the persistent kernel launch of the last successful
  * DEC_MODE_MIXED_BATCHED solve (the launch that solved every instance, not
@@ -461,8 +496,8 @@ dec_status dec_set_barrier_test(dec_ctx* ctx, int64_t spin_limit, int32_t withho
  * fixed 768 KiB array inside the library's device image, present on every
  * GPU that loads the library until the process exits; n_edges may therefore
  * not exceed 67,108,864 (DEC_ERR_LIMIT beyond).  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress) once; make
- * that first call before any stream capture.  Every call clears the counter
+ * looks up that array's device address (cudaGetSymbolAddress) once.  Every
+ * call clears the counter
  * and reuses the same array, so calls that overlap on the GPU (other
  * streams, other host threads, on the same device) race: serialise them.
  * The call returns after out3 is written.  No cudaMalloc or cudaFree is

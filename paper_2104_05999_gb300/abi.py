@@ -36,6 +36,7 @@ DEC_MODE_FP64, DEC_MODE_MIXED, DEC_MODE_MIXED_PHASED, DEC_MODE_MIXED_BATCHED = 0
 DEC_KERNEL_SPMV_F64, DEC_KERNEL_SPMV_F32 = 0, 1
 DEC_KERNEL_FSAI_F64, DEC_KERNEL_FSAI_BF16 = 2, 3
 DEC_CRACK_MAX_FLUX, DEC_CRACK_ORDER, DEC_CRACK_REBUILD = 0, 1, 16
+DEC_GEOM_FP64, DEC_GEOM_MIXED = 0, 1
 
 _P = C.c_void_p
 _I64 = C.c_int64
@@ -69,6 +70,9 @@ SIGNATURES = {
     "dec_time_kernel": [_P, _I32, _I32, _I64, _P],
     "dec_get_launch_count": [_P, _P],
     "dec_set_barrier_test": [_P, _I64, _I32],
+    "dec_set_geom_precision": [_P, _I32],
+    "dec_set_batch_variant": [_P, _I32],
+    "dec_get_geom_fp64_tets": [_P, _P],
     "dec_k_eff_edges_noalloc": [C.c_int, _P, _P, _I64, _P, _P, _P, _P, _P],
 }
 
@@ -285,6 +289,21 @@ class Context:
         v = C.c_int32()
         self._check(self.lib.dec_get_batch_variant(self.h, C.byref(v)))
         return v.value
+
+    def dec_set_geom_precision(self, precision):
+        """DEC_GEOM_FP64 or DEC_GEOM_MIXED for the next Hodge assemblies."""
+        self._check(self.lib.dec_set_geom_precision(self.h, int(precision)))
+
+    def dec_get_geom_fp64_tets(self):
+        """Tets the last Hodge assembly computed in FP64."""
+        v = C.c_int64()
+        self._check(self.lib.dec_get_geom_fp64_tets(self.h, C.byref(v)))
+        return v.value
+
+    def dec_set_batch_variant(self, variant=0):
+        """Force a batched launch variant (a dec_get_batch_variant code; 0:
+        autotune)."""
+        self._check(self.lib.dec_set_batch_variant(self.h, int(variant)))
 
     def dec_get_crack_iterations(self):
         """CG iterations summed over the steps of the last crack growth."""

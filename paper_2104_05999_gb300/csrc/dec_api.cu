@@ -378,6 +378,15 @@ dec_status dec_crack_evolve(dec_ctx* ctx, int32_t rule, int32_t max_steps,
   return st;
 }
 
+dec_status dec_set_batch_variant(dec_ctx* ctx, int32_t variant) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (variant != 0 && !dec::batch_variant_code(variant))
+    return ctx->fail(DEC_ERR_ARG, "set_batch_variant: unknown variant");
+  ctx->batch_force = variant;
+  return DEC_OK;
+}
+
 dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries) {
   if (!ctx) return DEC_ERR_ARG;
   ctx->err.clear();
@@ -582,6 +591,21 @@ dec_status dec_tet_whitney(dec_ctx* ctx, double* v) {
   DEC_TRY_STATUS(dec::tet_whitney(ctx, ctx->tet_flux ? ctx->tflux.p : nullptr, ctx->tr.p));
   DEC_TRY(download(v, (const double*)ctx->tr.p, 3 * ctx->m, s));
   DEC_TRY(cudaStreamSynchronize(s));
+  return DEC_OK;
+}
+
+dec_status dec_set_geom_precision(dec_ctx* ctx, int32_t precision) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  if (precision != DEC_GEOM_FP64 && precision != DEC_GEOM_MIXED)
+    return ctx->fail(DEC_ERR_ARG, "set_geom_precision: unknown precision");
+  ctx->geom_precision = precision;
+  return DEC_OK;
+}
+
+dec_status dec_get_geom_fp64_tets(const dec_ctx* ctx, int64_t* n_tets) {
+  if (!ctx || !n_tets) return DEC_ERR_ARG;
+  *n_tets = ctx->geom_fp64_tets;
   return DEC_OK;
 }
 

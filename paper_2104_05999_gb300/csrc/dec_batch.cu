@@ -224,6 +224,28 @@ __device__ __forceinline__ void gather_wait() {
 template <int U>
 constexpr int gather_smem() { return U * kBBlock * (int)sizeof(float4); }
 
+// Staged variants (Dirichlet sets): every warp streams the structure of its
+// slices through a private double buffer in shared memory, K entries of its
+// C rows per chunk; the 16-byte cp.async copies of the next chunk (of this
+// slice, or of the warp's slice in the block's next window) are in flight
+// while the current chunk's gathers run, so a row waits for its structure
+// once per slice instead of once per few entries.  A chunk holds at most
+// K * C * 8 bytes (an L entry: column and FP32 value; an FSAI entry: column
+// and BF16 value).
+__device__ __forceinline__ void copy16_async(void* dst, const void* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void copy_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void copy_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+template <int K>
+constexpr int stage_smem(int C) { return 2 * kBWarps * K * C * 8; }
+
 // Structure of one L entry: column and its raw weight data (value bits;
 // for crack states also the first crack state; for fields the four
 // instances' weights).
@@ -467,9 +489,10 @@ struct Acc2 {
 // The vector phases run in element order: element e of a [n][BS] vector
 // seen as float4s belongs to quad e % TPR, and with a stride that is a
 // multiple of 1024 every thread stays on its own quad q = lane % TPR.
-template <int KIND, int U, bool SMEM, bool PIPE>
+template <int KIND, int U, bool SMEM, bool PIPE, int STAGE = 0>
 __global__ void __launch_bounds__(kBBlock, 1)
 pcg_batched_persistent(BatchArgs a) {
+  static_assert(STAGE == 0 || (KIND == kSets && !SMEM), "staging: Dirichlet sets only");
   // barrier test: bar[3] != 0 withholds the last block, so the others'
   // first barrier wait runs out (DEC_ERR_TIMEOUT)
   if (*(volatile unsigned*)(a.bar + 3) && blockIdx.x == gridDim.x - 1) return;
@@ -496,6 +519,15 @@ pcg_batched_persistent(BatchArgs a) {
   auto act = [&](const int* flags, int j) { return flags[kIPT * q + j] != 0; };
   auto any4 = [&](const int* flags) {
     return flags[kIPT * q] | flags[kIPT * q + 1] | flags[kIPT * q + 2] | flags[kIPT * q + 3];
+  };
+  // whether a row-product phase runs for this lane: per lane (its quad has
+  // an instance in `flags`), or, in the staged variants, whose warps copy
+  // and synchronise together, for the whole warp (any lane's quad); the
+  // extra lanes then compute products for instances that are not iterating,
+  // which no later step reads (their step length is 0, their p is kept)
+  auto phase_on = [&](const int* flags) {
+    if constexpr (STAGE > 0) return __any_sync(0xffffffffu, any4(flags)) != 0;
+    else return any4(flags) != 0;
   };
   // the slices of this block: one per warp in each window it owns.  Slices
   // are sorted by length inside a window, so the warp-to-slice assignment
@@ -572,6 +604,148 @@ pcg_batched_persistent(BatchArgs a) {
       l2_prefetch(a.Gb[h] + b0 * BS, 2 * BS * (b1 - b0), a.Gb[h], a.Gb[h] + a.Gtotal[h] * BS);
     else
       l2_prefetch(a.Gv[h] + b0, 2 * (b1 - b0), a.Gv[h], a.Gv[h] + a.Gtotal[h]);
+  };
+  // Staged streaming (STAGE = K entries per chunk): the windows and
+  // prefetches of windows_pf; the structure arrays A0 (eb0 bytes per entry)
+  // and A1 (eb1, or none) of each slice go through the warp's double buffer.
+  // consume(chunk, nent, acc) adds nent entries of the chunk (A0's part at
+  // offset 0, A1's at K * C * eb0) to the row's accumulators; finish(row,
+  // acc) completes a row.  Every lane of a warp takes the same path.
+  auto staged = [&](const int32_t* perm, const int32_t* sptr, auto&& pf_struct,
+                    const float4* V0, const float4* V1, const char* A0, int eb0,
+                    const char* A1, int eb1, auto&& consume, auto&& finish) {
+    int64_t win = blockIdx.x;
+    if (win >= a.nwin) return;
+    extern __shared__ __align__(16) float4 bsm_slots[];
+    const int chunk = STAGE * C * 8;
+    char* wb = reinterpret_cast<char*>(bsm_slots) + (size_t)warp * 2 * chunk;
+    auto copy_chunk = [&](int32_t b0, int j0, int nent, int buf) {
+      char* d = wb + buf * chunk;
+      const char* s0 = A0 + ((int64_t)b0 + (int64_t)C * j0) * eb0;
+      const int n0 = nent * C * eb0 / 16;
+      for (int i = lane; i < n0; i += 32) copy16_async(d + 16 * i, s0 + 16 * i);
+      if (A1) {
+        const char* s1 = A1 + ((int64_t)b0 + (int64_t)C * j0) * eb1;
+        char* d1 = d + STAGE * C * eb0;
+        const int n1 = nent * C * eb1 / 16;
+        for (int i = lane; i < n1; i += 32) copy16_async(d1 + 16 * i, s1 + 16 * i);
+      }
+    };
+    int k = 0;
+    auto slice_of = [&](int64_t w, int kk) {
+      return w * kBWarps + ((warp + 13 * kk) & (kBWarps - 1));
+    };
+    int64_t s = slice_of(win, 0);
+    int32_t row = __ldg(perm + s * C + r), b0 = __ldg(sptr + s);
+    int32_t W = (__ldg(sptr + s + 1) - b0) / C;
+    int cb = 0;
+    bool have = false;          // this slice's first chunk is already in buffer cb
+    for (;;) {
+      const int64_t nxt = win + gridDim.x;
+      int32_t row2 = -1, c0 = 0, W2 = 0;
+      if (nxt < a.nwin) {
+        const int64_t s2 = slice_of(nxt, k + 1);
+        row2 = __ldg(perm + s2 * C + r);
+        c0 = __ldg(sptr + s2);
+        W2 = (__ldg(sptr + s2 + 1) - c0) / C;
+        if (lane == 0) {
+          pf_struct(s2);
+          if (V0) pf_rows(V0, nxt);
+          if (V1) pf_rows(V1, nxt);
+        }
+      }
+      float acc[kIPT] = {0.f, 0.f, 0.f, 0.f};
+      bool next_have = false;
+      if (W > 0) {
+        if (!have) {
+          copy_chunk(b0, 0, min(STAGE, W), cb);
+          copy_commit();
+        }
+        for (int j0 = 0; j0 < W; j0 += STAGE) {
+          const int nent = min(STAGE, W - j0);
+          next_have = false;
+          if (j0 + STAGE < W) {
+            copy_chunk(b0, j0 + STAGE, min(STAGE, W - j0 - STAGE), cb ^ 1);
+          } else if (W2 > 0) {
+            copy_chunk(c0, 0, min(STAGE, W2), cb ^ 1);
+            next_have = true;
+          }
+          copy_commit();
+          copy_wait<1>();
+          __syncwarp();
+          consume(wb + cb * chunk, nent, acc);
+          __syncwarp();
+          cb ^= 1;
+        }
+      }
+      have = next_have;
+      finish(row, acc);
+      if (nxt >= a.nwin) break;
+      win = nxt;
+      ++k;
+      row = row2;
+      b0 = c0;
+      W = W2;
+    }
+    copy_wait<0>();
+    __syncwarp();
+  };
+  // chunk consumers of the staged variants: L of Dirichlet sets ((column,
+  // FP32 value) pairs) and an FSAI half (columns, then BF16 values), in
+  // entry order with the FMAs of l_row / g_row, so results are bit-identical
+  auto consume_L = [=](const float4* __restrict__ Xv, const char* ch, int nent,
+                       float (&acc)[kIPT]) {
+    const int2* e = reinterpret_cast<const int2*>(ch);
+    for (int u0 = 0; u0 < nent; u0 += U) {
+      float4 xv[U];
+      float wv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        wv[u] = 0.0f;
+        xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (u0 + u < nent) {
+          const int2 cw = e[(u0 + u) * C + r];
+          wv[u] = __int_as_float(cw.y);
+          xv[u] = Xv[(int64_t)cw.x * TPR + q];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u0 + u < nent) {
+          acc[0] = fmaf(wv[u], xv[u].x, acc[0]);
+          acc[1] = fmaf(wv[u], xv[u].y, acc[1]);
+          acc[2] = fmaf(wv[u], xv[u].z, acc[2]);
+          acc[3] = fmaf(wv[u], xv[u].w, acc[3]);
+        }
+      }
+    }
+  };
+  auto consume_G = [=](const float4* __restrict__ Xv, const char* ch, int nent,
+                       float (&acc)[kIPT]) {
+    const int32_t* col = reinterpret_cast<const int32_t*>(ch);
+    const __nv_bfloat16* gv = reinterpret_cast<const __nv_bfloat16*>(ch + STAGE * C * 4);
+    for (int u0 = 0; u0 < nent; u0 += U) {
+      float4 xv[U];
+      float gw[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        gw[u] = 0.0f;
+        xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (u0 + u < nent) {
+          gw[u] = __bfloat162float(gv[(u0 + u) * C + r]);
+          xv[u] = Xv[(int64_t)col[(u0 + u) * C + r] * TPR + q];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u0 + u < nent) {
+          acc[0] = fmaf(gw[u], xv[u].x, acc[0]);
+          acc[1] = fmaf(gw[u], xv[u].y, acc[1]);
+          acc[2] = fmaf(gw[u], xv[u].z, acc[2]);
+          acc[3] = fmaf(gw[u], xv[u].w, acc[3]);
+        }
+      }
+    }
   };
   // device time of the phases of the FP32 iterations, taken by thread 0 of
   // block 0 as it leaves each grid barrier (every block leaves a barrier at
@@ -657,25 +831,49 @@ pcg_batched_persistent(BatchArgs a) {
 
   // z = M r = G^T (G r) on the instances in `flags`, with r.z per instance
   auto apply_precond = [&](const int* flags, bool timed) -> bool {
-    if (any4(flags))
-      windows_pf(a.Gperm[0], a.Gsptr[0], [&](int64_t sn) { pf_G(0, sn); }, R, nullptr,
-                 [&](int32_t base, int32_t W, int32_t row) {
-        const float4 y = g_row<U, SMEM, PIPE>(a, 0, base, W, r, q, row, R);
-        if (row >= 0) T[(int64_t)row * TPR + q] = y;
-      });
+    if (phase_on(flags)) {
+      if constexpr (STAGE > 0) {
+        staged(a.Gperm[0], a.Gsptr[0], [&](int64_t sn) { pf_G(0, sn); }, R, nullptr,
+               reinterpret_cast<const char*>(a.Gcol[0]), 4,
+               reinterpret_cast<const char*>(a.Gv[0]), 2,
+               [&](const char* ch, int nent, float (&y)[kIPT]) { consume_G(R, ch, nent, y); },
+               [&](int32_t row, float (&y)[kIPT]) {
+          if (row >= 0) T[(int64_t)row * TPR + q] = make_float4(y[0], y[1], y[2], y[3]);
+        });
+      } else {
+        windows_pf(a.Gperm[0], a.Gsptr[0], [&](int64_t sn) { pf_G(0, sn); }, R, nullptr,
+                   [&](int32_t base, int32_t W, int32_t row) {
+          const float4 y = g_row<U, SMEM, PIPE>(a, 0, base, W, r, q, row, R);
+          if (row >= 0) T[(int64_t)row * TPR + q] = y;
+        });
+      }
+    }
     if (!bgrid_sync(a.bar, err)) return false;
     if (timed) mark(2);
     Acc2 acc[kIPT];
-    if (any4(flags))
-      windows_pf(a.Gperm[1], a.Gsptr[1], [&](int64_t sn) { pf_G(1, sn); }, T, R,
-                 [&](int32_t base, int32_t W, int32_t row) {
-        const float4 zi = g_row<U, SMEM, PIPE>(a, 1, base, W, r, q, row, T);
+    if (phase_on(flags)) {
+      auto upper_row = [&](int32_t row, const float4 zi) {
         if (row < 0) return;
         Z[(int64_t)row * TPR + q] = zi;
         const float4 ri = R[(int64_t)row * TPR + q];
 #pragma unroll
         for (int j = 0; j < kIPT; ++j) acc[j].add(get4(ri, j), get4(zi, j));
-      });
+      };
+      if constexpr (STAGE > 0) {
+        staged(a.Gperm[1], a.Gsptr[1], [&](int64_t sn) { pf_G(1, sn); }, T, R,
+               reinterpret_cast<const char*>(a.Gcol[1]), 4,
+               reinterpret_cast<const char*>(a.Gv[1]), 2,
+               [&](const char* ch, int nent, float (&y)[kIPT]) { consume_G(T, ch, nent, y); },
+               [&](int32_t row, float (&y)[kIPT]) {
+          upper_row(row, make_float4(y[0], y[1], y[2], y[3]));
+        });
+      } else {
+        windows_pf(a.Gperm[1], a.Gsptr[1], [&](int64_t sn) { pf_G(1, sn); }, T, R,
+                   [&](int32_t base, int32_t W, int32_t row) {
+          upper_row(row, g_row<U, SMEM, PIPE>(a, 1, base, W, r, q, row, T));
+        });
+      }
+    }
     double v[kIPT];
 #pragma unroll
     for (int j = 0; j < kIPT; ++j) v[j] = acc[j].get();
@@ -710,16 +908,33 @@ pcg_batched_persistent(BatchArgs a) {
     for (;;) {
       {
         Acc2 acc[kIPT];
-        if (any4(S.iterating))
-          windows_pf(a.Lperm, a.Lsptr, pf_L, Pv, nullptr,
-                     [&](int32_t base, int32_t W, int32_t row) {
-            const float4 qi = l_row<KIND, U, SMEM, PIPE>(a, base, W, r, q, row, st, Pv);
+        if (phase_on(S.iterating)) {
+          auto spmm_row = [&](int32_t row, const float4 qi) {
             if (row < 0) return;
             Q[(int64_t)row * TPR + q] = qi;
             const float4 pi = Pv[(int64_t)row * TPR + q];
 #pragma unroll
             for (int j = 0; j < kIPT; ++j) acc[j].add(get4(pi, j), get4(qi, j));
-          });
+          };
+          if constexpr (STAGE > 0) {
+            // CSR form of the Dirichlet sets: L_ii x_i + the staged entries
+            staged(a.Lperm, a.Lsptr, pf_L, Pv, nullptr, reinterpret_cast<const char*>(a.Lcw),
+                   8, nullptr, 0,
+                   [&](const char* ch, int nent, float (&y)[kIPT]) { consume_L(Pv, ch, nent, y); },
+                   [&](int32_t row, float (&y)[kIPT]) {
+              const int32_t rr = row >= 0 ? row : 0;
+              const float4 xi = Pv[(int64_t)rr * TPR + q];
+              const float d = a.d32[rr];
+              spmm_row(row, make_float4(fmaf(d, xi.x, y[0]), fmaf(d, xi.y, y[1]),
+                                        fmaf(d, xi.z, y[2]), fmaf(d, xi.w, y[3])));
+            });
+          } else {
+            windows_pf(a.Lperm, a.Lsptr, pf_L, Pv, nullptr,
+                       [&](int32_t base, int32_t W, int32_t row) {
+              spmm_row(row, l_row<KIND, U, SMEM, PIPE>(a, base, W, r, q, row, st, Pv));
+            });
+          }
+        }
         double v[kIPT];
 #pragma unroll
         for (int j = 0; j < kIPT; ++j) v[j] = acc[j].get();
@@ -1389,13 +1604,32 @@ dec_status batch_refresh_values(dec_ctx* ctx) {
 }
 
 // Kernel variants for the context's instance kind: entries per round trip
-// (U), whether the next round's structure loads overlap the gathers, and
-// where the gathers go (registers or shared memory); reported as
-// 100 * shared + 10 * overlapped + U.  All variants of a kind add a row's
-// entries in the same order, so the choice never changes a result.
-constexpr int kNumGatherVariants = 5;
-constexpr int kGatherVariants[kNumGatherVariants] = {2, 4, 12, 114, 106};
-constexpr int kGatherSmem[kNumGatherVariants] = {0, 0, 0, gather_smem<4>(), gather_smem<6>()};
+// (U), whether the next round's structure loads overlap the gathers, where
+// the gathers go (registers or shared memory), and for Dirichlet sets the
+// staged variants (structure through shared memory, K entries per chunk);
+// reported as 1000 * K / 8 + 100 * shared + 10 * overlapped + U.  All
+// variants of a kind add a row's entries in the same order, so the choice
+// never changes a result.
+constexpr int kNumGatherVariants = 8;
+constexpr int kGatherVariants[kNumGatherVariants] = {2, 4, 12, 114, 106, 1004, 2004, 2002};
+constexpr int kStageEntries[kNumGatherVariants] = {0, 0, 0, 0, 0, 8, 16, 16};
+
+bool batch_variant_code(int code) {
+  for (int c = 0; c < kNumGatherVariants; ++c)
+    if (kGatherVariants[c] == code) return true;
+  return false;
+}
+
+static int variant_smem(int v, int C) {
+  switch (v) {
+    case 3: return gather_smem<4>();
+    case 4: return gather_smem<6>();
+    case 5: return stage_smem<8>(C);
+    case 6:
+    case 7: return stage_smem<16>(C);
+    default: return 0;
+  }
+}
 
 template <int KIND>
 static const void* batch_kernel(int v) {
@@ -1404,8 +1638,18 @@ static const void* batch_kernel(int v) {
     case 1: return (const void*)pcg_batched_persistent<KIND, 4, false, false>;
     case 2: return (const void*)pcg_batched_persistent<KIND, 2, false, true>;
     case 3: return (const void*)pcg_batched_persistent<KIND, 4, true, true>;
-    default: return (const void*)pcg_batched_persistent<KIND, 6, true, false>;
+    case 4: return (const void*)pcg_batched_persistent<KIND, 6, true, false>;
+    default: break;
   }
+  if constexpr (KIND == kSets) {
+    switch (v) {
+      case 5: return (const void*)pcg_batched_persistent<KIND, 4, false, false, 8>;
+      case 6: return (const void*)pcg_batched_persistent<KIND, 4, false, false, 16>;
+      case 7: return (const void*)pcg_batched_persistent<KIND, 2, false, false, 16>;
+      default: break;
+    }
+  }
+  return nullptr;
 }
 
 dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
@@ -1425,13 +1669,18 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
               : kind == kStates ? batch_kernel<kStates>(v)
                                 : batch_kernel<kFields>(v);
   bool usable[kNumGatherVariants];
+  int smem[kNumGatherVariants];
   bool any = false;
+  const int Cb = 32 / (BS / kIPT);
   for (int v = 0; v < kNumGatherVariants; ++v) {
+    smem[v] = variant_smem(v, Cb);
+    usable[v] = false;
+    // staged copies move 16 bytes: C rows of a BF16 value must fill them
+    if (!kern[v] || (kStageEntries[v] > 0 && Cb < 8)) continue;
     int per_sm = 0;
     DEC_TRY(cudaFuncSetAttribute(kern[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kGatherSmem[v]));
-    DEC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[v], kBBlock,
-                                                          kGatherSmem[v]));
+                                 smem[v]));
+    DEC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[v], kBBlock, smem[v]));
     usable[v] = per_sm >= 1;
     any = any || usable[v];
   }
@@ -1498,8 +1747,7 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
     cudaError_t e = cudaMemsetAsync(ctx->coop.p, 0, sizeof(int64_t) * (16 + 3 * kBMax), s);
     if (e == cudaSuccess) e = write_barrier_test(ctx, bar);
     if (e == cudaSuccess)
-      e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args,
-                                      kGatherSmem[v], s);
+      e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args, smem[v], s);
     ctx->launches += 1;
     return e;
   };
@@ -1512,6 +1760,14 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
   // same mesh uploaded again, as a benchmark or a time loop does)
   const bool same = ctx->batch_tune_key[slot][0] == n && ctx->batch_tune_key[slot][1] == ctx->nnz;
   int v = same ? ctx->batch_variant[slot] - 1 : -1;
+  if (ctx->batch_force != 0) {
+    // a variant chosen by the caller (dec_set_batch_variant): no tuning
+    v = -1;
+    for (int c = 0; c < kNumGatherVariants; ++c)
+      if (kGatherVariants[c] == ctx->batch_force && usable[c]) v = c;
+    if (v < 0)
+      return ctx->fail(DEC_ERR_ARG, "batched solve: the chosen variant does not fit this batch");
+  }
   if (v < 0) {
     constexpr int kTuneIters = 8;
     cudaEvent_t e0, e1;
@@ -1559,8 +1815,7 @@ dec_status solve_batched(dec_ctx* ctx, double rtol, int max_iter, int* iters,
     cudaError_t e = cudaMemsetAsync(ctx->coop.p, 0, sizeof(int64_t) * (16 + 3 * kBMax), s);
     if (e == cudaSuccess) e = write_barrier_test(ctx, bar);
     if (e == cudaSuccess)
-      e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args,
-                                      kGatherSmem[v], s);
+      e = cudaLaunchCooperativeKernel(kern[v], dim3(grid), dim3(kBBlock), args, smem[v], s);
     ctx->launches += 1;
     DEC_TRY(e);
   }

@@ -32,16 +32,42 @@
 
 namespace dec {
 
-struct V3 {
-  double x, y, z;
+template <typename T>
+struct Vec3 {
+  T x, y, z;
 };
+using V3 = Vec3<double>;
+using F3 = Vec3<float>;
 __device__ __forceinline__ V3 mk(double x, double y, double z) { return {x, y, z}; }
-__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
-__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
-__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator+(Vec3<T> a, Vec3<T> b) {
+  return {a.x + b.x, a.y + b.y, a.z + b.z};
+}
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator-(Vec3<T> a, Vec3<T> b) {
+  return {a.x - b.x, a.y - b.y, a.z - b.z};
+}
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator*(T s, Vec3<T> a) {
+  return {s * a.x, s * a.y, s * a.z};
+}
+template <typename T>
+__device__ __forceinline__ T dot(Vec3<T> a, Vec3<T> b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename T>
+__device__ __forceinline__ Vec3<T> cross(Vec3<T> a, Vec3<T> b) {
   return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Tet circumcentre relative to vertex 0, from the edge vectors R[1..3]:
+// (|a|^2 (b x c) + |b|^2 (c x a) + |c|^2 (a x b)) / (2 a.(b x c))
+template <typename T>
+__device__ __forceinline__ Vec3<T> tet_circumcentre(const Vec3<T> (&R)[4]) {
+  const Vec3<T> bxc = cross(R[2], R[3]), cxa = cross(R[3], R[1]), axb = cross(R[1], R[2]);
+  const T det6 = dot(R[1], bxc);
+  return (T(0.5) / det6) * (dot(R[1], R[1]) * bxc + dot(R[2], R[2]) * cxa +
+                            dot(R[3], R[3]) * axb);
 }
 
 // circumcentre of triangle (p, p+a, p+b): p + ((|a|^2 b - |b|^2 a) x (a x b)) / (2 |a x b|^2)
@@ -109,11 +135,53 @@ __constant__ int kEdgeB[6] = {1, 2, 3, 2, 3, 3};
 __constant__ int kEdgeC[6] = {2, 1, 1, 0, 0, 0};  // the two other vertices
 __constant__ int kEdgeD[6] = {3, 3, 2, 3, 2, 1};
 
-__global__ void __launch_bounds__(128)
+// The two halves of every slot's piece of dual face (below), from the edge
+// vectors R[1..3] of the tet (R[0] = 0): the circumcentre cT and, per face,
+// H[v] = signed distance from c_T to the face opposite v (+ towards v)
+// divided by twice the face area, ((c_T - x).N) / |N|^2 with N the inward
+// normal.  Half of the dual face of edge (a,b) inside face F = {a,b,c} is
+// the right triangle (m_e, c_F, c_T) with legs |e|/2 * cot(angle at c) and
+// the distance from c_T to F; with cot = (x_a-x_c).(x_b-x_c) / |N_F| its
+// area over |e| is (1/4) (x_a-x_c).(x_b-x_c) * H_F.
+template <typename T>
+__device__ __forceinline__ void tet_pieces(const Vec3<T> (&R)[4], Vec3<T>& cT, T (&a0)[6],
+                                           T (&a1)[6]) {
+  cT = tet_circumcentre(R);
+  T H[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int i0 = (v + 1) & 3, i1 = (v + 2) & 3, i2 = (v + 3) & 3;
+    const Vec3<T> nn = cross(R[i1] - R[i0], R[i2] - R[i0]);
+    const T side = dot(nn, R[v] - R[i0]);
+    const T h = dot(cT - R[i0], nn) / dot(nn, nn);
+    H[v] = side > T(0) ? h : -h;
+  }
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    const int ea = kEdgeA[s], eb = kEdgeB[s], ec = kEdgeC[s], ed = kEdgeD[s];
+    const T cot_c = dot(R[ea] - R[ec], R[eb] - R[ec]);   // face opposite d
+    const T cot_d = dot(R[ea] - R[ed], R[eb] - R[ed]);   // face opposite c
+    a0[s] = T(0.25) * cot_c * H[ed];
+    a1[s] = T(0.25) * cot_d * H[ec];
+  }
+}
+
+// Shape bound of the FP32 geometry (DEC_GEOM_MIXED): a tet is computed in
+// FP32 when L^3 <= kShapeMax |6 V|, L the longest of its edges from vertex 0
+// (a regular tet has 2.8, a Kuhn tet 5.2; 96 % of the tets of a jittered
+// Delaunay cube pass 16), in FP64 otherwise.
+constexpr float kShapeMax = 16.0f;
+
+// MIXED = false: every tet in FP64.  MIXED = true: well-shaped tets in FP32.
+// n_fp64 counts the tets computed in FP64.
+template <bool MIXED>
+__global__ void __launch_bounds__(128, 3)
 hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tets,
                  const double* __restrict__ kcond, int64_t m,
                  double* __restrict__ piece, double* __restrict__ kpart,
-                 uint8_t* __restrict__ slot_cut, DiscGrid grid) {
+                 uint8_t* __restrict__ slot_cut, DiscGrid grid,
+                 unsigned long long* __restrict__ n_fp64) {
+  unsigned n64 = 0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
        t += (int64_t)gridDim.x * blockDim.x) {
     int4 v4 = reinterpret_cast<const int4*>(tets)[t];
@@ -125,41 +193,56 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
                 xyz[3 * (int64_t)vid[i] + 2]);
     const double kT = kcond ? kcond[t] : 1.0;
     const int64_t q6 = 6 * m;
-    // all vectors relative to X[0]
-    V3 R[4];
-    R[0] = mk(0.0, 0.0, 0.0);
+    V3 cT;                 // circumcentre relative to X[0]
+    double a0[6], a1[6];
+    double Et = 0.0;       // bound on the error of cT (FP32 geometry)
+    bool fast = false;
+    if constexpr (MIXED) {
+      // edge vectors formed in FP64 and rounded once: each coordinate
+      // carries a relative error of at most 2^-24
+      F3 Rf[4];
+      Rf[0] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int i = 1; i < 4; ++i) R[i] = X[i] - X[0];
-    // tet circumcentre: (|a|^2 (b x c) + |b|^2 (c x a) + |c|^2 (a x b)) / (2 a.(b x c))
-    const V3 bxc = cross(R[2], R[3]), cxa = cross(R[3], R[1]), axb = cross(R[1], R[2]);
-    const double det6 = dot(R[1], bxc);
-    const V3 cT = (0.5 / det6) * (dot(R[1], R[1]) * bxc + dot(R[2], R[2]) * cxa +
-                                  dot(R[3], R[3]) * axb);
-    // H[v]: signed distance from c_T to the face opposite v (+ towards v),
-    // divided by twice the face area: ((c_T - x).N) / |N|^2, N = inward normal
-    double H[4];
+      for (int i = 1; i < 4; ++i)
+        Rf[i] = {(float)(X[i].x - X[0].x), (float)(X[i].y - X[0].y),
+                 (float)(X[i].z - X[0].z)};
+      const float det6 = fabsf(dot(Rf[1], cross(Rf[2], Rf[3])));
+      const float L2 = fmaxf(dot(Rf[1], Rf[1]), fmaxf(dot(Rf[2], Rf[2]), dot(Rf[3], Rf[3])));
+      const float L = sqrtf(L2);
+      if (L2 * L <= kShapeMax * det6) {
+        fast = true;
+        F3 cTf;
+        float b0[6], b1[6];
+        tet_pieces(Rf, cTf, b0, b1);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int i0 = (v + 1) & 3, i1 = (v + 2) & 3, i2 = (v + 3) & 3;
-      const V3 nn = cross(R[i1] - R[i0], R[i2] - R[i0]);
-      const double side = dot(nn, R[v] - R[i0]);
-      const double h = dot(cT - R[i0], nn) / dot(nn, nn);
-      H[v] = side > 0.0 ? h : -h;
+        for (int s = 0; s < 6; ++s) {
+          a0[s] = b0[s];
+          a1[s] = b1[s];
+        }
+        cT = mk(cTf.x, cTf.y, cTf.z);
+        // With rho = L^3 / |6V| the rounded edge vectors move the
+        // circumcentre (the solution of 2 R c = |R_i|^2, whose matrix has
+        // smallest singular value >= |6V| / (3 L^2)) by at most
+        // (17 rho + 24 rho^2) u L; the formula's own roundings are of the same
+        // order.  Et doubles the sum (u = 2^-24).
+        const double rho = (double)(L2 * L) / (double)det6;
+        Et = 64.0 * 5.9604645e-8 * rho * (1.0 + rho) * (double)L;
+      }
     }
-    // Half of the dual face of edge (a,b) inside face F = {a,b,c}: right
-    // triangle (m_e, c_F, c_T) with legs |e|/2 * cot(angle at c) and the
-    // distance from c_T to F.  With cot = (x_a-x_c).(x_b-x_c) / |N_F| its
-    // area over |e| is (1/4) (x_a-x_c).(x_b-x_c) * H_F.
+    if (!fast) {
+      V3 R[4];
+      R[0] = mk(0.0, 0.0, 0.0);
+#pragma unroll
+      for (int i = 1; i < 4; ++i) R[i] = X[i] - X[0];
+      tet_pieces(R, cT, a0, a1);
+      ++n64;
+    }
     uint8_t first[6];
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
-      const int ea = kEdgeA[s], eb = kEdgeB[s], ec = kEdgeC[s], ed = kEdgeD[s];
-      const double cot_c = dot(R[ea] - R[ec], R[eb] - R[ec]);   // face opposite d
-      const double cot_d = dot(R[ea] - R[ed], R[eb] - R[ed]);   // face opposite c
-      const double a0 = 0.25 * cot_c * H[ed], a1 = 0.25 * cot_d * H[ec];
-      piece[t * 6 + s] = a0 + a1;
+      piece[t * 6 + s] = a0[s] + a1[s];
       if (kcond) {                       // unsigned part of the face, with and without k
-        const double u = fabs(a0) + fabs(a1);
+        const double u = fabs(a0[s]) + fabs(a1[s]);
         kpart[t * 6 + s] = kT * u;
         kpart[q6 + t * 6 + s] = u;
       }
@@ -172,9 +255,21 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
       // the candidate discs are those binned in the cells the ball's box
       // meets.  The radius carries a relative margin; the cut decision
       // itself stays exact.
+      // With FP32 geometry the ball is centred on the rounded circumcentre
+      // and its radius grows by twice the error bound, so it still holds the
+      // exact ball; the exact circumcentre cTx is then formed in FP64 for a
+      // tet that some disc may cut.
       const V3 cTa = X[0] + cT;
-      const double RT2 = dot(cT, cT) * (1.0 + 1e-9) + 1e-300;
-      const double RT = sqrt(RT2);
+      double RT2, RT;
+      if (fast) {
+        RT = (sqrt(dot(cT, cT)) + 2.0 * Et) * (1.0 + 1e-9);
+        RT2 = RT * RT;
+      } else {
+        RT2 = dot(cT, cT) * (1.0 + 1e-9) + 1e-300;
+        RT = sqrt(RT2);
+      }
+      V3 cTx = cTa;
+      bool have_cTx = !fast;
       const double lo[3] = {cTa.x - RT, cTa.y - RT, cTa.z - RT};
       const double hi[3] = {cTa.x + RT, cTa.y + RT, cTa.z + RT};
       // face circumcentres: only for a tet that some disc may cut
@@ -242,7 +337,15 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
             cF[v] = tri_circumcentre(X[(v + 1) & 3], X[(v + 2) & 3], X[(v + 3) & 3]);
           have_cF = true;
         }
-        const double sT = dot(cTa - dc, dn);
+        if (!have_cTx) {
+          V3 R[4];
+          R[0] = mk(0.0, 0.0, 0.0);
+#pragma unroll
+          for (int i = 1; i < 4; ++i) R[i] = X[i] - X[0];
+          cTx = X[0] + tet_circumcentre(R);
+          have_cTx = true;
+        }
+        const double sT = dot(cTx - dc, dn);
         double sF[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) sF[v] = dot(cF[v] - dc, dn);
@@ -257,7 +360,7 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
             const double sf = sF[opp];
             if ((sM > 0.0 && sf > 0.0 && sT > 0.0) || (sM < 0.0 && sf < 0.0 && sT < 0.0))
               continue;                                   // no crossing: rho = inf
-            const double rho = crack_rho_s(me, cF[opp], cTa, sM, sf, sT, dc);
+            const double rho = crack_rho_s(me, cF[opp], cTx, sM, sf, sT, dc);
             for (int st = 0; st < (int)first[s]; ++st)
               if (rho <= grid.scales[st] * r) {
                 first[s] = (uint8_t)st;
@@ -286,6 +389,9 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
 #pragma unroll
     for (int s = 0; s < 6; ++s) slot_cut[t * 6 + s] = first[s];
   }
+  // tets computed in FP64: one atomic per warp
+  const unsigned w64 = __reduce_add_sync(0xffffffffu, n64);
+  if ((threadIdx.x & 31) == 0 && w64) atomicAdd(n_fp64, (unsigned long long)w64);
 }
 
 // *1[e] = sum of the pieces of e (already divided by |e|), in increasing
@@ -490,10 +596,19 @@ dec_status assemble_hodge(dec_ctx* ctx, int64_t nd, bool has_k, int n_fields) {
   }
   int64_t blocks = (m + 127) / 128;
   if (blocks > (int64_t)ctx->num_sms * 64) blocks = (int64_t)ctx->num_sms * 64;
-  hodge_tet_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 128, 0, s>>>(
+  DEC_TRY(ctx->geom_count.ensure(1));
+  DEC_TRY(cudaMemsetAsync(ctx->geom_count.p, 0, sizeof(unsigned long long), s));
+  auto* kern = ctx->geom_precision == DEC_GEOM_MIXED ? hodge_tet_kernel<true>
+                                                     : hodge_tet_kernel<false>;
+  kern<<<(unsigned)std::max<int64_t>(blocks, 1), 128, 0, s>>>(
       ctx->xyz.p, ctx->tets.p, has_k ? ctx->kcond.p : nullptr,
-      m, ctx->piece.p, has_k ? ctx->piece.p + q : nullptr, ctx->slot_cut.p, g);
+      m, ctx->piece.p, has_k ? ctx->piece.p + q : nullptr, ctx->slot_cut.p, g,
+      ctx->geom_count.p);
   DEC_TRY(cudaGetLastError());
+  unsigned long long n64 = 0;
+  DEC_TRY(cudaMemcpyAsync(&n64, ctx->geom_count.p, sizeof(n64), cudaMemcpyDeviceToHost, s));
+  DEC_TRY(cudaStreamSynchronize(s));
+  ctx->geom_fp64_tets = (int64_t)n64;
   int64_t eb = (ctx->ne + 255) / 256;
   if (eb > (int64_t)ctx->num_sms * 32) eb = (int64_t)ctx->num_sms * 32;
   edge_reduce_kernel<<<(unsigned)std::max<int64_t>(eb, 1), 256, 0, s>>>(

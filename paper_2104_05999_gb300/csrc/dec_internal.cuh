@@ -124,6 +124,9 @@ struct dec_ctx {
   dec::DevBuf<uint8_t> first_cut;  // [ne]
   dec::DevBuf<double> discs;       // [nd][7]
   dec::DevBuf<float> discs_f;      // [nd][8]: FP32 copy for the crack pre-test
+  dec::DevBuf<unsigned long long> geom_count;   // tets of the last assembly done in FP64
+  int geom_precision = DEC_GEOM_FP64;           // dec_set_geom_precision
+  int64_t geom_fp64_tets = 0;
   dec::DevBuf<double> scales;      // [n_scales]
   dec::DevBuf<int32_t> grid_start, grid_items;
   dec::DevBuf<double> kcond;       // [m]
@@ -175,6 +178,7 @@ struct dec_ctx {
   int batch_variant[4] = {0, 0, 0, 0};     // tuned variant + 1 per stride 8..64
   int64_t batch_tune_key[4][2] = {};       // (n, nnz) each choice was tuned for
   int batch_variant_used = -1;             // variant of the last batched solve
+  int batch_force = 0;                     // dec_set_batch_variant (0: autotune)
   double batch_kernel_ms = -1.0;           // device time of its persistent launch
   double batch_phase_ms[6] = {};           // its per-phase times and FP32 iterations
   int64_t crack_iters = 0;                 // CG iterations of the last crack growth
@@ -199,7 +203,7 @@ struct dec_ctx {
     seg_pay.release(); seg_start.release(); key_a.release(); key_b.release();
     val_a.release(); val_b.release(); hist.release(); scan_tmp.release();
     flags.release(); errflag.release(); piece.release(); slot_cut.release();
-    w.release(); first_cut.release(); discs.release(); discs_f.release(); scales.release();
+    w.release(); first_cut.release(); discs.release(); discs_f.release(); geom_count.release(); scales.release();
     grid_start.release(); grid_items.release(); kcond.release(); rowptr.release();
     col.release(); eid.release(); dpos.release(); up_begin.release();
     lo_begin.release(); pos_up.release(); lo_col.release(); lo_eid.release();
@@ -412,6 +416,7 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
 cudaError_t init_kernel_attributes();
 // crack growth
 // the tet-centred form
+bool batch_variant_code(int code);
 dec_status tet_faces(dec_ctx* ctx);
 dec_status tet_solve(dec_ctx* ctx, const double* T0_dev, double kappa, double limiter,
                      const int32_t* cracked_dev, int64_t n_cracked, const double* flux_dev,

@@ -71,7 +71,9 @@ extern "C" dec_status dec_k_eff_edges_noalloc(int device, void* stream,
   using namespace dec;
   if (!E || !w || !T || !xyz || !node_tag || !out3 || n_edges < 1) return DEC_ERR_ARG;
   if (n_edges > kNaMaxEdges) return DEC_ERR_LIMIT;
-  if (device < 0 || device >= 64) return DEC_ERR_ARG;
+  int n_devices = 0;
+  if (cudaGetDeviceCount(&n_devices) != cudaSuccess) return DEC_ERR_CUDA;
+  if (device < 0 || device >= 64 || device >= n_devices) return DEC_ERR_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return DEC_ERR_CUDA;
   double* scratch = nullptr;
   {

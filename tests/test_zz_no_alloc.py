@@ -34,13 +34,21 @@ def test_noalloc_k_eff_matches_context_entry_point_twice():
     d_E, d_w, d_T = t(E), t(w), t(res.T[0])
     d_xyz, d_tag = t(wl.xyz), t(wl.tags)
     torch.cuda.synchronize()
-    for _ in range(2):
+    for call in range(2):
+        free0 = torch.cuda.mem_get_info(0)[0]
         got = abi.dec_k_eff_edges_noalloc(0, d_E, d_w, d_T, d_xyz, d_tag)
         # same sums in another order: FP64 rounding only
         np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-14)
+        if call == 1:      # the first call may load the module's code
+            assert torch.cuda.mem_get_info(0)[0] == free0
     # a size beyond the fixed scratch is refused before any launch
     out = np.zeros(3)
     st = abi.load().dec_k_eff_edges_noalloc(
         0, None, d_E.data_ptr(), 67108864 + 1, d_w.data_ptr(), d_T.data_ptr(),
         d_xyz.data_ptr(), d_tag.data_ptr(), out.ctypes.data)
     assert st == abi.DEC_ERR_LIMIT
+    # a device index beyond the devices present is an argument error
+    st = abi.load().dec_k_eff_edges_noalloc(
+        torch.cuda.device_count(), None, d_E.data_ptr(), 10, d_w.data_ptr(),
+        d_T.data_ptr(), d_xyz.data_ptr(), d_tag.data_ptr(), out.ctypes.data)
+    assert st == abi.DEC_ERR_ARG
