@@ -443,6 +443,9 @@ def gpu_arm(args, rank, world):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(round(launches)),
         "geom_mixed": geom_mixed,
+        # launch shapes the single-instance autotuner picked (L, FSAI halves)
+        "sell_shapes": {"fp64": list(ctx.dec_get_sell_variant(0)),
+                        "fp32": list(ctx.dec_get_sell_variant(1))},
         "batch_variant": ctx.dec_get_batch_variant() if want == "batched" else None,
         "batch_phase_ms": ([round(float(x), 4) for x in ctx.dec_get_batch_phase_ms()]
                            if want == "batched" else None),

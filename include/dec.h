@@ -245,11 +245,32 @@ dec_status dec_k_eff(dec_ctx* ctx, double* q_in, double* q_out, double* energy);
  *                   sets of 8 or 16 instances only) + 100 * (gathers into
  *                   shared memory by cp.async) + 10 * (next entries'
  *                   structure loaded while the gathers are in flight) +
- *                   gathers per round trip: one of 2, 4, 12, 114, 106,
- *                   1004, 2004, 2002.
+ *                   gathers per round trip, + 500 when only the FSAI halves
+ *                   are staged (the SpMM as variant 12): one of 2, 4, 12,
+ *                   114, 106, 1004, 2004, 2002, 2512.
  * All variants give bit-identical results.  DEC_ERR_STATE before the first
  * batched solve.  (No counterpart in the paper: a launch-shape choice.) */
 dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries);
+
+/* Launch shapes of the single-instance SELL kernels (the L product of
+ * DEC_MODE_FP64 and of the per-phase mixed modes, and the two FSAI halves),
+ * as picked by their autotuner: the first such solve of a problem size
+ * (nodes, matrix entries) in a precision times a few launches of every
+ * shape on the context's scratch vectors and keeps the fastest.
+ *   precision  0: FP64 (DEC_MODE_FP64), 1: FP32 / BF16 (mixed modes).
+ *   l_shape    host: 100 * (resident blocks per SM) + (matrix entries per
+ *              round trip): one of 408, 808, 412, 804; 0 before any solve.
+ *   g_shape    host: 14 (slices staged in shared memory) or 8 (round trips
+ *              of 8 entries); 0 before any solve with FSAI.
+ * Every shape gives bit-identical results.  (No counterpart in the paper:
+ * a launch-shape choice.) */
+dec_status dec_get_sell_variant(const dec_ctx* ctx, int32_t precision, int32_t* l_shape,
+                                int32_t* g_shape);
+
+/* Make the following single-instance solves use the given shapes (codes of
+ * dec_get_sell_variant; 0: the autotuner's choice, tuned again at the next
+ * solve).  Errors: DEC_ERR_ARG for an unknown code. */
+dec_status dec_set_sell_variant(dec_ctx* ctx, int32_t l_shape, int32_t g_shape);
 
 /* Make the following batched solves of the context use one variant (a code
  * of dec_get_batch_variant) instead of the autotuner's choice; 0 returns to

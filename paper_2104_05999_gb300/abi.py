@@ -72,6 +72,8 @@ SIGNATURES = {
     "dec_set_barrier_test": [_P, _I64, _I32],
     "dec_set_geom_precision": [_P, _I32],
     "dec_set_batch_variant": [_P, _I32],
+    "dec_set_sell_variant": [_P, _I32, _I32],
+    "dec_get_sell_variant": [_P, _I32, _P, _P],
     "dec_get_geom_fp64_tets": [_P, _P],
     "dec_k_eff_edges_noalloc": [C.c_int, _P, _P, _I64, _P, _P, _P, _P, _P],
 }
@@ -304,6 +306,17 @@ class Context:
         """Force a batched launch variant (a dec_get_batch_variant code; 0:
         autotune)."""
         self._check(self.lib.dec_set_batch_variant(self.h, int(variant)))
+
+    def dec_set_sell_variant(self, l_shape=0, g_shape=0):
+        """Force the single-instance SELL launch shapes (0: autotune)."""
+        self._check(self.lib.dec_set_sell_variant(self.h, int(l_shape), int(g_shape)))
+
+    def dec_get_sell_variant(self, precision):
+        """(L shape, FSAI shape) codes in use for precision 0 (FP64) or 1."""
+        a, b = C.c_int32(), C.c_int32()
+        self._check(self.lib.dec_get_sell_variant(self.h, int(precision), C.byref(a),
+                                                  C.byref(b)))
+        return a.value, b.value
 
     def dec_get_crack_iterations(self):
         """CG iterations summed over the steps of the last crack growth."""

@@ -387,6 +387,29 @@ dec_status dec_set_batch_variant(dec_ctx* ctx, int32_t variant) {
   return DEC_OK;
 }
 
+dec_status dec_set_sell_variant(dec_ctx* ctx, int32_t l_shape, int32_t g_shape) {
+  if (!ctx) return DEC_ERR_ARG;
+  ctx->err.clear();
+  const int vl = l_shape == 0 ? -1 : dec::sell_l_index(l_shape);
+  const int vg = g_shape == 0 ? -1 : dec::sell_g_index(g_shape);
+  if ((l_shape != 0 && vl < 0) || (g_shape != 0 && vg < 0))
+    return ctx->fail(DEC_ERR_ARG, "set_sell_variant: unknown shape");
+  ctx->sell_force_l = vl;
+  ctx->sell_force_g = vg;
+  // a return to the autotuner tunes again at the next solve
+  if (vl < 0 || vg < 0)
+    for (auto& k : ctx->sell_key) k[0] = k[1] = 0;
+  return DEC_OK;
+}
+
+dec_status dec_get_sell_variant(const dec_ctx* ctx, int32_t precision, int32_t* l_shape,
+                                int32_t* g_shape) {
+  if (!ctx || !l_shape || !g_shape || (precision != 0 && precision != 1)) return DEC_ERR_ARG;
+  *l_shape = dec::sell_l_code(ctx->sell_l[precision]);
+  *g_shape = dec::sell_g_code(ctx->sell_g[precision]);
+  return DEC_OK;
+}
+
 dec_status dec_get_batch_variant(dec_ctx* ctx, int32_t* gather_entries) {
   if (!ctx) return DEC_ERR_ARG;
   ctx->err.clear();

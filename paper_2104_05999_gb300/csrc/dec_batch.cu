@@ -229,9 +229,9 @@ constexpr int gather_smem() { return U * kBBlock * (int)sizeof(float4); }
 // C rows per chunk; the 16-byte cp.async copies of the next chunk (of this
 // slice, or of the warp's slice in the block's next window) are in flight
 // while the current chunk's gathers run, so a row waits for its structure
-// once per slice instead of once per few entries.  A chunk holds at most
-// K * C * 8 bytes (an L entry: column and FP32 value; an FSAI entry: column
-// and BF16 value).
+// once per slice instead of once per few entries.  A chunk holds K * C * 8
+// bytes when L is staged too (an L entry: column and FP32 value), K * C * 6
+// when only the FSAI halves are (column and BF16 value).
 __device__ __forceinline__ void copy16_async(void* dst, const void* src) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
@@ -244,7 +244,9 @@ __device__ __forceinline__ void copy_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 template <int K>
-constexpr int stage_smem(int C) { return 2 * kBWarps * K * C * 8; }
+constexpr int stage_smem(int C, int entry_bytes = 8) {
+  return 2 * kBWarps * K * C * entry_bytes;
+}
 
 // Structure of one L entry: column and its raw weight data (value bits;
 // for crack states also the first crack state; for fields the four
@@ -489,7 +491,11 @@ struct Acc2 {
 // The vector phases run in element order: element e of a [n][BS] vector
 // seen as float4s belongs to quad e % TPR, and with a stride that is a
 // multiple of 1024 every thread stays on its own quad q = lane % TPR.
-template <int KIND, int U, bool SMEM, bool PIPE, int STAGE = 0>
+// STAGE > 0: the FSAI halves (and, with STAGE_L, the SpMM) stream their
+// structure through shared memory in chunks of STAGE entries, UG gathers
+// per round trip; the other row products use U, SMEM and PIPE.
+template <int KIND, int U, bool SMEM, bool PIPE, int STAGE = 0, bool STAGE_L = true,
+          int UG = U>
 __global__ void __launch_bounds__(kBBlock, 1)
 pcg_batched_persistent(BatchArgs a) {
   static_assert(STAGE == 0 || (KIND == kSets && !SMEM), "staging: Dirichlet sets only");
@@ -617,7 +623,7 @@ pcg_batched_persistent(BatchArgs a) {
     int64_t win = blockIdx.x;
     if (win >= a.nwin) return;
     extern __shared__ __align__(16) float4 bsm_slots[];
-    const int chunk = STAGE * C * 8;
+    const int chunk = STAGE * C * (STAGE_L ? 8 : 6);
     char* wb = reinterpret_cast<char*>(bsm_slots) + (size_t)warp * 2 * chunk;
     auto copy_chunk = [&](int32_t b0, int j0, int nent, int buf) {
       char* d = wb + buf * chunk;
@@ -696,11 +702,11 @@ pcg_batched_persistent(BatchArgs a) {
   auto consume_L = [=](const float4* __restrict__ Xv, const char* ch, int nent,
                        float (&acc)[kIPT]) {
     const int2* e = reinterpret_cast<const int2*>(ch);
-    for (int u0 = 0; u0 < nent; u0 += U) {
-      float4 xv[U];
-      float wv[U];
+    for (int u0 = 0; u0 < nent; u0 += UG) {
+      float4 xv[UG];
+      float wv[UG];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
+      for (int u = 0; u < UG; ++u) {
         wv[u] = 0.0f;
         xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (u0 + u < nent) {
@@ -710,7 +716,7 @@ pcg_batched_persistent(BatchArgs a) {
         }
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
+      for (int u = 0; u < UG; ++u) {
         if (u0 + u < nent) {
           acc[0] = fmaf(wv[u], xv[u].x, acc[0]);
           acc[1] = fmaf(wv[u], xv[u].y, acc[1]);
@@ -724,11 +730,11 @@ pcg_batched_persistent(BatchArgs a) {
                        float (&acc)[kIPT]) {
     const int32_t* col = reinterpret_cast<const int32_t*>(ch);
     const __nv_bfloat16* gv = reinterpret_cast<const __nv_bfloat16*>(ch + STAGE * C * 4);
-    for (int u0 = 0; u0 < nent; u0 += U) {
-      float4 xv[U];
-      float gw[U];
+    for (int u0 = 0; u0 < nent; u0 += UG) {
+      float4 xv[UG];
+      float gw[UG];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
+      for (int u = 0; u < UG; ++u) {
         gw[u] = 0.0f;
         xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (u0 + u < nent) {
@@ -737,7 +743,7 @@ pcg_batched_persistent(BatchArgs a) {
         }
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
+      for (int u = 0; u < UG; ++u) {
         if (u0 + u < nent) {
           acc[0] = fmaf(gw[u], xv[u].x, acc[0]);
           acc[1] = fmaf(gw[u], xv[u].y, acc[1]);
@@ -916,7 +922,7 @@ pcg_batched_persistent(BatchArgs a) {
 #pragma unroll
             for (int j = 0; j < kIPT; ++j) acc[j].add(get4(pi, j), get4(qi, j));
           };
-          if constexpr (STAGE > 0) {
+          if constexpr (STAGE > 0 && STAGE_L) {
             // CSR form of the Dirichlet sets: L_ii x_i + the staged entries
             staged(a.Lperm, a.Lsptr, pf_L, Pv, nullptr, reinterpret_cast<const char*>(a.Lcw),
                    8, nullptr, 0,
@@ -1607,12 +1613,15 @@ dec_status batch_refresh_values(dec_ctx* ctx) {
 // (U), whether the next round's structure loads overlap the gathers, where
 // the gathers go (registers or shared memory), and for Dirichlet sets the
 // staged variants (structure through shared memory, K entries per chunk);
-// reported as 1000 * K / 8 + 100 * shared + 10 * overlapped + U.  All
-// variants of a kind add a row's entries in the same order, so the choice
-// never changes a result.
-constexpr int kNumGatherVariants = 8;
-constexpr int kGatherVariants[kNumGatherVariants] = {2, 4, 12, 114, 106, 1004, 2004, 2002};
-constexpr int kStageEntries[kNumGatherVariants] = {0, 0, 0, 0, 0, 8, 16, 16};
+// reported as 1000 * K / 8 + 100 * shared + 10 * overlapped + U, plus 500
+// when only the FSAI halves are staged (the SpMM then runs as the variant
+// 10 * overlapped + U, the staged halves with 4 gathers per round trip).
+// All variants of a kind add a row's entries in the same order, so the
+// choice never changes a result.
+constexpr int kNumGatherVariants = 9;
+constexpr int kGatherVariants[kNumGatherVariants] = {2,    4,    12,   114, 106,
+                                                     1004, 2004, 2002, 2512};
+constexpr int kStageEntries[kNumGatherVariants] = {0, 0, 0, 0, 0, 8, 16, 16, 16};
 
 bool batch_variant_code(int code) {
   for (int c = 0; c < kNumGatherVariants; ++c)
@@ -1627,6 +1636,7 @@ static int variant_smem(int v, int C) {
     case 5: return stage_smem<8>(C);
     case 6:
     case 7: return stage_smem<16>(C);
+    case 8: return stage_smem<16>(C, 6);   // FSAI entries only
     default: return 0;
   }
 }
@@ -1646,6 +1656,7 @@ static const void* batch_kernel(int v) {
       case 5: return (const void*)pcg_batched_persistent<KIND, 4, false, false, 8>;
       case 6: return (const void*)pcg_batched_persistent<KIND, 4, false, false, 16>;
       case 7: return (const void*)pcg_batched_persistent<KIND, 2, false, false, 16>;
+      case 8: return (const void*)pcg_batched_persistent<KIND, 2, false, true, 16, false, 4>;
       default: break;
     }
   }

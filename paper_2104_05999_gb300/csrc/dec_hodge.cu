@@ -82,7 +82,10 @@ __device__ __forceinline__ V3 tri_circumcentre(V3 p, V3 q, V3 r) {
 // the plane meets the closed triangle (P0, P1, P2); +inf when the plane misses
 // the triangle or contains it.
 // s0..s2 are the signed distances dot(P_i - c, nrm) of the three points.
-__device__ double crack_rho_s(V3 P0, V3 P1, V3 P2, double s0, double s1, double s2, V3 c) {
+// Not inlined: the exact test runs for few (tet, disc) pairs, and twelve
+// inlined copies made the kernel large enough to stall on instruction fetch.
+__device__ __noinline__ double crack_rho_s(V3 P0, V3 P1, V3 P2, double s0, double s1,
+                                           double s2, V3 c) {
   V3 P[3] = {P0, P1, P2};
   const double s[3] = {s0, s1, s2};
   int count = 0;
@@ -146,24 +149,69 @@ __constant__ int kEdgeD[6] = {3, 3, 2, 3, 2, 1};
 template <typename T>
 __device__ __forceinline__ void tet_pieces(const Vec3<T> (&R)[4], Vec3<T>& cT, T (&a0)[6],
                                            T (&a1)[6]) {
-  cT = tet_circumcentre(R);
+  // For a positively oriented tet the inward normals of the faces opposite
+  // vertices 1, 2, 3 are the cross products the circumcentre needs, and the
+  // one opposite vertex 0 is minus their sum; |N_v| is twice the face area.
+  const Vec3<T> bxc = cross(R[2], R[3]), cxa = cross(R[3], R[1]), axb = cross(R[1], R[2]);
+  const T det6 = dot(R[1], bxc);
+  const Vec3<T> N[4] = {T(-1) * (bxc + cxa + axb), bxc, cxa, axb};
+  T nn[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) nn[v] = dot(N[v], N[v]);
+  // 1 / det6 and 1 / |N_v|^2: in FP64 one division of their product and
+  // products of the others (the division is a long instruction sequence on
+  // GB300's narrow FP64 pipe); five divisions when the product leaves the
+  // normal range, and always in FP32
+  T inv_det, inv_nn[4];
+  bool direct = true;
+  if constexpr (sizeof(T) == sizeof(double)) {
+    const T p01 = det6 * nn[0], p012 = p01 * nn[1], p0123 = p012 * nn[2];
+    const T prod = p0123 * nn[3];
+    if (prod > 1e-280 && prod < 1e280) {
+      direct = false;
+      const T r = T(1) / prod;
+      const T s3 = nn[3], s23 = nn[2] * s3, s123 = nn[1] * s23;
+      inv_det = r * (nn[0] * s123);
+      inv_nn[0] = r * (det6 * s123);
+      inv_nn[1] = r * (p01 * s23);
+      inv_nn[2] = r * (p012 * s3);
+      inv_nn[3] = r * p0123;
+    }
+  }
+  if (direct) {
+    inv_det = T(1) / det6;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) inv_nn[v] = T(1) / nn[v];
+  }
+  cT = (T(0.5) * inv_det) * (dot(R[1], R[1]) * bxc + dot(R[2], R[2]) * cxa +
+                             dot(R[3], R[3]) * axb);
+  // H[v]: signed distance from c_T to the face opposite v (+ towards v)
+  // over twice the face area; faces 1-3 contain vertex 0 (R[0] = 0)
   T H[4];
+  H[0] = dot(cT - R[1], N[0]) * inv_nn[0];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int i0 = (v + 1) & 3, i1 = (v + 2) & 3, i2 = (v + 3) & 3;
-    const Vec3<T> nn = cross(R[i1] - R[i0], R[i2] - R[i0]);
-    const T side = dot(nn, R[v] - R[i0]);
-    const T h = dot(cT - R[i0], nn) / dot(nn, nn);
-    H[v] = side > T(0) ? h : -h;
-  }
-#pragma unroll
-  for (int s = 0; s < 6; ++s) {
-    const int ea = kEdgeA[s], eb = kEdgeB[s], ec = kEdgeC[s], ed = kEdgeD[s];
-    const T cot_c = dot(R[ea] - R[ec], R[eb] - R[ec]);   // face opposite d
-    const T cot_d = dot(R[ea] - R[ed], R[eb] - R[ed]);   // face opposite c
-    a0[s] = T(0.25) * cot_c * H[ed];
-    a1[s] = T(0.25) * cot_d * H[ec];
-  }
+  for (int v = 1; v < 4; ++v) H[v] = dot(cT, N[v]) * inv_nn[v];
+  // the six edge vectors; (x_a - x_c).(x_b - x_c) are dot products of two
+  // edges at vertex c.  Slot s joins local vertices (a, b); c and d are the
+  // other two (the slots of kEdgeA..D, spelled out so that every index is
+  // a compile-time constant and the vectors stay in registers).
+  const Vec3<T> E[4][4] = {
+      {R[0], R[1], R[2], R[3]},
+      {T(-1) * R[1], R[0], R[2] - R[1], R[3] - R[1]},
+      {T(-1) * R[2], R[1] - R[2], R[0], R[3] - R[2]},
+      {T(-1) * R[3], R[1] - R[3], R[2] - R[3], R[0]}};   // E[i][j] = x_j - x_i
+  auto slot = [&](int s, int a, int b, int c, int d) {
+    const T cot_c = dot(E[c][a], E[c][b]);   // face opposite d
+    const T cot_d = dot(E[d][a], E[d][b]);   // face opposite c
+    a0[s] = T(0.25) * cot_c * H[d];
+    a1[s] = T(0.25) * cot_d * H[c];
+  };
+  slot(0, 0, 1, 2, 3);
+  slot(1, 0, 2, 1, 3);
+  slot(2, 0, 3, 1, 2);
+  slot(3, 1, 2, 0, 3);
+  slot(4, 1, 3, 0, 2);
+  slot(5, 2, 3, 0, 1);
 }
 
 // Shape bound of the FP32 geometry (DEC_GEOM_MIXED): a tet is computed in
@@ -349,12 +397,12 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
         double sF[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) sF[v] = dot(cF[v] - dc, dn);
-#pragma unroll
+#pragma unroll 1
         for (int s = 0; s < 6; ++s) {
           if (first[s] == 0) continue;
           V3 me = 0.5 * (X[kEdgeA[s]] + X[kEdgeB[s]]);
           const double sM = dot(me - dc, dn);
-#pragma unroll
+#pragma unroll 1
           for (int h = 0; h < 2; ++h) {
             const int opp = h == 0 ? kEdgeD[s] : kEdgeC[s];
             const double sf = sF[opp];
@@ -372,18 +420,19 @@ hodge_tet_kernel(const double* __restrict__ xyz, const int32_t* __restrict__ tet
       if (!empty) {
         const int64_t ncell = (int64_t)(c1[0] - c0[0] + 1) * (c1[1] - c0[1] + 1) *
                               (c1[2] - c0[2] + 1);
-        if (ncell > grid.nd) {
-          // a far circumcentre (flat boundary tet): fewer tests without the grid
-          for (int id = 0; id < grid.nd; ++id) test_disc(id);
-        } else {
-          for (int gz = c0[2]; gz <= c1[2]; ++gz)
-            for (int gy = c0[1]; gy <= c1[1]; ++gy)
-              for (int gx = c0[0]; gx <= c1[0]; ++gx) {
-                const int cell = gx + grid.dim[0] * (gy + grid.dim[1] * gz);
-                for (int it = grid.start[cell]; it < grid.start[cell + 1]; ++it)
-                  test_disc(grid.items[it]);
-              }
-        }
+        // a far circumcentre (flat boundary tet): fewer tests without the
+        // grid, i.e. every disc once (one pass of the loops below); one call
+        // site of test_disc keeps the kernel small
+        const bool all = ncell > grid.nd;
+        if (all) c1[0] = c0[0], c1[1] = c0[1], c1[2] = c0[2];
+        for (int gz = c0[2]; gz <= c1[2]; ++gz)
+          for (int gy = c0[1]; gy <= c1[1]; ++gy)
+            for (int gx = c0[0]; gx <= c1[0]; ++gx) {
+              const int cell = gx + grid.dim[0] * (gy + grid.dim[1] * gz);
+              const int i0 = all ? 0 : grid.start[cell];
+              const int i1 = all ? grid.nd : grid.start[cell + 1];
+              for (int it = i0; it < i1; ++it) test_disc(all ? it : grid.items[it]);
+            }
       }
     }
 #pragma unroll

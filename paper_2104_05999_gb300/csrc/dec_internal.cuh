@@ -179,6 +179,11 @@ struct dec_ctx {
   int64_t batch_tune_key[4][2] = {};       // (n, nnz) each choice was tuned for
   int batch_variant_used = -1;             // variant of the last batched solve
   int batch_force = 0;                     // dec_set_batch_variant (0: autotune)
+  // launch shapes of the single-instance SELL kernels per precision
+  // (0: FP64, 1: FP32), tuned per (n, nnz), or forced (>= 0)
+  int sell_l[2] = {-1, -1}, sell_g[2] = {-1, -1};
+  int64_t sell_key[2][2] = {};
+  int sell_force_l = -1, sell_force_g = -1;
   double batch_kernel_ms = -1.0;           // device time of its persistent launch
   double batch_phase_ms[6] = {};           // its per-phase times and FP32 iterations
   int64_t crack_iters = 0;                 // CG iterations of the last crack growth
@@ -416,6 +421,10 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
 cudaError_t init_kernel_attributes();
 // crack growth
 // the tet-centred form
+int sell_l_code(int v);
+int sell_g_code(int v);
+int sell_l_index(int code);
+int sell_g_index(int code);
 bool batch_variant_code(int code);
 dec_status tet_faces(dec_ctx* ctx);
 dec_status tet_solve(dec_ctx* ctx, const double* T0_dev, double kappa, double limiter,

@@ -162,14 +162,14 @@ __device__ __forceinline__ void for_rows(const SellArg<MT>& A, const VT* __restr
   }
 }
 
-// q = A p and alpha = (r.z) / (p.q)
-template <int WMAX, typename MT, typename VT>
+// q = A p and alpha = (r.z) / (p.q); CHUNK entries per register round trip
+template <int WMAX, int CHUNK, typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock)
 spmv_pq_kernel(SellArg<MT> A, const VT* __restrict__ p, VT* __restrict__ q,
                CgScalars* cg, double* partial, unsigned* ticket) {
   if (*(volatile int*)&cg->done) return;
   double pq = 0.0;
-  for_rows<WMAX, kChunkL>(A, p, [&](int32_t r, VT acc) {
+  for_rows<WMAX, CHUNK>(A, p, [&](int32_t r, VT acc) {
     q[r] = acc;
     pq += to_d(p[r]) * to_d(acc);
   });
@@ -413,8 +413,9 @@ cudaError_t init_kernel_attributes() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   };
-  set((const void*)spmv_pq_kernel<kStageL, double, double>, sell_smem<kStageL, double>());
-  set((const void*)spmv_pq_kernel<kStageL, float, float>, sell_smem<kStageL, float>());
+  set((const void*)spmv_pq_kernel<kStageL, kChunkL, double, double>,
+      sell_smem<kStageL, double>());
+  set((const void*)spmv_pq_kernel<kStageL, kChunkL, float, float>, sell_smem<kStageL, float>());
   set((const void*)sell_apply_kernel<kStageG, double, double>, sell_smem<kStageG, double>());
   set((const void*)sell_apply_dot_kernel<kStageG, double, double>, sell_smem<kStageG, double>());
   set((const void*)sell_apply_kernel<kStageG, __nv_bfloat16, float>,
@@ -509,6 +510,130 @@ dec_status k_eff_all(dec_ctx* ctx, double* out3_host) {
   return DEC_OK;
 }
 
+// ------------------------------------------------------- launch shapes
+// The single-instance SELL kernels run in one of a few launch shapes,
+// picked at run time per problem size (nodes, matrix entries) and
+// precision by sell_tune: for L, register round trips of 4, 8 or 12
+// entries at 4 or 8 resident blocks per SM (code 100 * blocks + entries);
+// for the FSAI halves, staged slices (code 14) or register round trips of 8
+// (code 8).  Every shape adds a row's entries in the same order, so the
+// choice never changes a result.
+struct LShape {
+  int chunk, per_sm;
+};
+constexpr int kNumLShapes = 4;
+constexpr LShape kLShapes[kNumLShapes] = {{8, 4}, {8, 8}, {12, 4}, {4, 8}};
+constexpr int kNumGShapes = 2;
+constexpr int kGShapeCode[kNumGShapes] = {kStageG, 8};
+
+static int lshape_code(int v) { return 100 * kLShapes[v].per_sm + kLShapes[v].chunk; }
+
+static unsigned sell_grid_n(const dec_ctx* ctx, int64_t nslices, int per_sm) {
+  return (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((nslices + kBlock / 32 - 1) / (kBlock / 32),
+                           (int64_t)ctx->num_sms * per_sm));
+}
+
+template <typename MT, typename VT>
+static void launch_spmv_pq(dec_ctx* ctx, int v, const SellArg<MT>& A, const VT* p, VT* q,
+                           CgScalars* cg, double* part, unsigned* tk) {
+  static_assert(kStageL == 0, "L shapes are register round trips");
+  const unsigned g = sell_grid_n(ctx, A.nslices, kLShapes[v].per_sm);
+  cudaStream_t s = ctx->stream;
+  switch (kLShapes[v].chunk) {
+    case 4: spmv_pq_kernel<0, 4, MT, VT><<<g, kBlock, 0, s>>>(A, p, q, cg, part, tk); break;
+    case 12: spmv_pq_kernel<0, 12, MT, VT><<<g, kBlock, 0, s>>>(A, p, q, cg, part, tk); break;
+    default: spmv_pq_kernel<0, 8, MT, VT><<<g, kBlock, 0, s>>>(A, p, q, cg, part, tk); break;
+  }
+}
+
+// t = G r, then z = G^T t with r.z (beta as sell_apply_dot_kernel)
+template <typename PT, typename VT>
+static void launch_fsai(dec_ctx* ctx, int v, const SellArg<PT>& Glo, const SellArg<PT>& Gup,
+                        const VT* r, VT* t, VT* z, int init, CgScalars* cg, double* part,
+                        unsigned* tk) {
+  cudaStream_t s = ctx->stream;
+  if (v == 0) {
+    constexpr int SG = sell_smem<kStageG, PT>();
+    sell_apply_kernel<kStageG, PT, VT><<<sell_grid<kStageG, PT>(ctx, Glo.nslices), kBlock, SG,
+                                         s>>>(Glo, r, t, cg);
+    sell_apply_dot_kernel<kStageG, PT, VT><<<sell_grid<kStageG, PT>(ctx, Gup.nslices), kBlock,
+                                             SG, s>>>(Gup, t, r, z, init, cg, part, tk);
+  } else {
+    sell_apply_kernel<0, PT, VT><<<sell_grid_n(ctx, Glo.nslices, 4), kBlock, 0, s>>>(Glo, r, t,
+                                                                                    cg);
+    sell_apply_dot_kernel<0, PT, VT><<<sell_grid_n(ctx, Gup.nslices, 4), kBlock, 0, s>>>(
+        Gup, t, r, z, init, cg, part, tk);
+  }
+}
+
+// Autotuner of the shapes above: the first phased solve of a problem size in
+// a precision (0: FP64, 1: FP32 / BF16) times 3 launches of each shape
+// (after one untimed) on the context's scratch vectors and keeps the
+// fastest; a shape set by dec_set_sell_variant is used instead.
+template <typename MT, typename PT, typename VT>
+static dec_status sell_tune(dec_ctx* ctx, int prec, const SellArg<MT>& A,
+                            const SellArg<PT>& Glo, const SellArg<PT>& Gup, bool fsai,
+                            VT* v0, VT* v1, VT* v2) {
+  if (ctx->sell_force_l >= 0) ctx->sell_l[prec] = ctx->sell_force_l;
+  if (ctx->sell_force_g >= 0) ctx->sell_g[prec] = ctx->sell_force_g;
+  const bool same = ctx->sell_key[prec][0] == ctx->n && ctx->sell_key[prec][1] == ctx->nnz;
+  const bool need_l = ctx->sell_force_l < 0 && (!same || ctx->sell_l[prec] < 0);
+  const bool need_g = fsai && ctx->sell_force_g < 0 && (!same || ctx->sell_g[prec] < 0);
+  if (!need_l && !need_g) return DEC_OK;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n;
+  DEC_TRY(cudaMemsetAsync(v0, 0, sizeof(VT) * n, s));
+  CgScalars h{};
+  h.rz = 1.0;
+  cudaEvent_t e0, e1;
+  DEC_TRY(cudaEventCreate(&e0));
+  DEC_TRY(cudaEventCreate(&e1));
+  auto timed = [&](auto&& launch, float* ms) -> dec_status {
+    float tot = 0.0f;
+    for (int rep = 0; rep < 4; ++rep) {
+      DEC_TRY(cudaMemcpyAsync(ctx->cg.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+      DEC_TRY(cudaEventRecord(e0, s));
+      launch();
+      DEC_TRY(cudaEventRecord(e1, s));
+      DEC_TRY(cudaEventSynchronize(e1));
+      float m = 0.0f;
+      DEC_TRY(cudaEventElapsedTime(&m, e0, e1));
+      if (rep > 0) tot += m;
+    }
+    *ms = tot;
+    return DEC_OK;
+  };
+  dec_status st = DEC_OK;
+  if (need_l) {
+    float best = 0.0f;
+    for (int v = 0; v < kNumLShapes && st == DEC_OK; ++v) {
+      float ms = 0.0f;
+      st = timed([&] { launch_spmv_pq<MT, VT>(ctx, v, A, v0, v1, ctx->cg.p, ctx->partial.p,
+                                             ctx->ticket.p); }, &ms);
+      ctx->launches += 4;
+      if (v == 0 || ms < best) { best = ms; ctx->sell_l[prec] = v; }
+    }
+  }
+  if (need_g && st == DEC_OK) {
+    float best = 0.0f;
+    for (int v = 0; v < kNumGShapes && st == DEC_OK; ++v) {
+      float ms = 0.0f;
+      st = timed([&] { launch_fsai<PT, VT>(ctx, v, Glo, Gup, v0, v1, v2, 1, ctx->cg.p,
+                                           ctx->partial.p, ctx->ticket.p); }, &ms);
+      ctx->launches += 8;
+      if (v == 0 || ms < best) { best = ms; ctx->sell_g[prec] = v; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DEC_OK) return st;
+  DEC_TRY(cudaGetLastError());
+  ctx->sell_key[prec][0] = ctx->n;
+  ctx->sell_key[prec][1] = ctx->nnz;
+  return DEC_OK;
+}
+
 // ------------------------------------------------------------- driver
 constexpr int kChunk = 16;       // iterations per graph launch / host poll
 
@@ -526,26 +651,22 @@ static void launch_iterations(dec_ctx* ctx, int64_t n, const Ops<MT, PT, DT>& op
                               int count) {
   cudaStream_t s = ctx->stream;
   const unsigned G = (unsigned)ctx->grid_vec;
-  const unsigned GA = sell_grid<kStageL, MT>(ctx, op.A.nslices);
-  const unsigned GL = sell_grid<kStageG, PT>(ctx, op.Glo.nslices);
-  const unsigned GU = sell_grid<kStageG, PT>(ctx, op.Gup.nslices);
-  constexpr int SA = sell_smem<kStageL, MT>(), SG = sell_smem<kStageG, PT>();
+  const int prec = sizeof(VT) == sizeof(double) ? 0 : 1;
+  const int vl = std::max(ctx->sell_l[prec], 0), vg = std::max(ctx->sell_g[prec], 0);
   CgScalars* cg = ctx->cg.p;
   double* part = ctx->partial.p;
   unsigned* tk = ctx->ticket.p;
   const bool jac = ctx->precond == DEC_PRECOND_JACOBI;
   ctx->launches += (int64_t)count * (jac ? 3 : 5);
   for (int it = 0; it < count; ++it) {
-    spmv_pq_kernel<kStageL, MT, VT><<<GA, kBlock, SA, s>>>(op.A, p, q, cg, part, tk);
+    launch_spmv_pq<MT, VT>(ctx, vl, op.A, p, q, cg, part, tk);
     if (jac) {
       update_kernel<VT, DT, true><<<G, kBlock, 0, s>>>(n, x, r, p, q, op.dinv, z,
                                                        max_iter, cg, part, tk);
     } else {
       update_kernel<VT, DT, false><<<G, kBlock, 0, s>>>(n, x, r, p, q, op.dinv, z,
                                                         max_iter, cg, part, tk);
-      sell_apply_kernel<kStageG, PT, VT><<<GL, kBlock, SG, s>>>(op.Glo, r, t, cg);
-      sell_apply_dot_kernel<kStageG, PT, VT><<<GU, kBlock, SG, s>>>(op.Gup, t, r, z, 0, cg,
-                                                                    part, tk);
+      launch_fsai<PT, VT>(ctx, vg, op.Glo, op.Gup, r, t, z, 0, cg, part, tk);
     }
     xpay_kernel<VT><<<G, kBlock, 0, s>>>(n, z, p, cg);
   }
@@ -559,18 +680,15 @@ static void launch_restart(dec_ctx* ctx, int64_t n, const Ops<MT, PT, DT>& op, V
                            VT* z, VT* p, VT* t, int init = 1) {
   cudaStream_t s = ctx->stream;
   const unsigned G = (unsigned)ctx->grid_vec;
-  constexpr int SG = sell_smem<kStageG, PT>();
+  const int prec = sizeof(VT) == sizeof(double) ? 0 : 1;
   CgScalars* cg = ctx->cg.p;
   ctx->launches += ctx->precond == DEC_PRECOND_JACOBI ? 2 : 3;
   if (ctx->precond == DEC_PRECOND_JACOBI) {
     jacobi_init_kernel<VT, DT><<<G, kBlock, 0, s>>>(n, op.dinv, r, z, init, cg,
                                                     ctx->partial.p, ctx->ticket.p);
   } else {
-    sell_apply_kernel<kStageG, PT, VT><<<sell_grid<kStageG, PT>(ctx, op.Glo.nslices), kBlock,
-                                         SG, s>>>(op.Glo, r, t, cg);
-    sell_apply_dot_kernel<kStageG, PT, VT><<<sell_grid<kStageG, PT>(ctx, op.Gup.nslices),
-                                             kBlock, SG, s>>>(op.Gup, t, r, z, init, cg,
-                                                              ctx->partial.p, ctx->ticket.p);
+    launch_fsai<PT, VT>(ctx, std::max(ctx->sell_g[prec], 0), op.Glo, op.Gup, r, t, z, init,
+                        cg, ctx->partial.p, ctx->ticket.p);
   }
   xpay_kernel<VT><<<G, kBlock, 0, s>>>(n, z, p, cg);
 }
@@ -634,6 +752,7 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
         fsai ? nullptr : ctx->dinv64.p + (int64_t)vs * n};
     double *x = ctx->x64.p, *r = ctx->r64.p, *z = ctx->z64.p, *p = ctx->p64.p,
            *q = ctx->q64.p, *t = ctx->t64.p;
+    DEC_TRY_STATUS(sell_tune(ctx, 0, op.A, op.Glo, op.Gup, fsai, t, q, z));
     if (warm) {
       // start from the current solution u: r = b - L u
       DEC_TRY(cudaMemcpyAsync(x, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -694,6 +813,7 @@ dec_status solve_instance(dec_ctx* ctx, int inst, double rtol, int max_iter,
     double* r64 = ctx->r64.p;
     float *x = ctx->x32.p, *r = ctx->r32.p, *z = ctx->z32.p, *p = ctx->p32.p,
           *q = ctx->q32.p, *t = ctx->t32.p;
+    DEC_TRY_STATUS(sell_tune(ctx, 1, op.A, op.Glo, op.Gup, fsai, t, q, z));
     // x64 = 0 (or the current solution u for a warm start)
     if (warm) DEC_TRY(cudaMemcpyAsync(x64, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     else DEC_TRY(cudaMemsetAsync(x64, 0, sizeof(double) * n, s));
@@ -788,37 +908,24 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
     DEC_TRY(cudaMemcpyAsync(&ctx->cg.p->done, &h.done, sizeof(int), cudaMemcpyHostToDevice, s));
     DEC_TRY(cudaEventRecord(e0, s));
     switch (which) {
+      // the shapes the autotuner picked (the defaults before any solve)
       case DEC_KERNEL_SPMV_F64:
-        spmv_pq_kernel<kStageL, double, double>
-            <<<sell_grid<kStageL, double>(ctx, L64.nslices), kBlock,
-               sell_smem<kStageL, double>(), s>>>(L64, ctx->p64.p, ctx->q64.p, ctx->cg.p,
-                                                  ctx->partial.p, ctx->ticket.p);
+        launch_spmv_pq<double, double>(ctx, std::max(ctx->sell_l[0], 0), L64, ctx->p64.p,
+                                       ctx->q64.p, ctx->cg.p, ctx->partial.p, ctx->ticket.p);
         break;
       case DEC_KERNEL_SPMV_F32:
-        spmv_pq_kernel<kStageL, float, float>
-            <<<sell_grid<kStageL, float>(ctx, L32.nslices), kBlock,
-               sell_smem<kStageL, float>(), s>>>(L32, ctx->p32.p, ctx->q32.p, ctx->cg.p,
-                                                 ctx->partial.p, ctx->ticket.p);
+        launch_spmv_pq<float, float>(ctx, std::max(ctx->sell_l[1], 0), L32, ctx->p32.p,
+                                     ctx->q32.p, ctx->cg.p, ctx->partial.p, ctx->ticket.p);
         break;
       case DEC_KERNEL_FSAI_F64:
-        sell_apply_kernel<kStageG, double, double>
-            <<<sell_grid<kStageG, double>(ctx, Glo64.nslices), kBlock,
-               sell_smem<kStageG, double>(), s>>>(Glo64, ctx->r64.p, ctx->t64.p, ctx->cg.p);
-        sell_apply_dot_kernel<kStageG, double, double>
-            <<<sell_grid<kStageG, double>(ctx, Gup64.nslices), kBlock,
-               sell_smem<kStageG, double>(), s>>>(Gup64, ctx->t64.p, ctx->r64.p, ctx->z64.p,
-                                                  1, ctx->cg.p, ctx->partial.p, ctx->ticket.p);
+        launch_fsai<double, double>(ctx, std::max(ctx->sell_g[0], 0), Glo64, Gup64,
+                                    ctx->r64.p, ctx->t64.p, ctx->z64.p, 1, ctx->cg.p,
+                                    ctx->partial.p, ctx->ticket.p);
         break;
       case DEC_KERNEL_FSAI_BF16:
-        sell_apply_kernel<kStageG, __nv_bfloat16, float>
-            <<<sell_grid<kStageG, __nv_bfloat16>(ctx, Glo16.nslices), kBlock,
-               sell_smem<kStageG, __nv_bfloat16>(), s>>>(Glo16, ctx->r32.p, ctx->t32.p,
-                                                         ctx->cg.p);
-        sell_apply_dot_kernel<kStageG, __nv_bfloat16, float>
-            <<<sell_grid<kStageG, __nv_bfloat16>(ctx, Gup16.nslices), kBlock,
-               sell_smem<kStageG, __nv_bfloat16>(), s>>>(Gup16, ctx->t32.p, ctx->r32.p,
-                                                         ctx->z32.p, 1, ctx->cg.p,
-                                                         ctx->partial.p, ctx->ticket.p);
+        launch_fsai<__nv_bfloat16, float>(ctx, std::max(ctx->sell_g[1], 0), Glo16, Gup16,
+                                          ctx->r32.p, ctx->t32.p, ctx->z32.p, 1, ctx->cg.p,
+                                          ctx->partial.p, ctx->ticket.p);
         break;
       default:
         st = ctx->fail(DEC_ERR_ARG, "time_kernel: unknown kernel id");
@@ -837,4 +944,19 @@ dec_status time_kernel(dec_ctx* ctx, int which, int reps, size_t flush_bytes,
   return st;
 }
 
+}  // namespace dec
+
+namespace dec {
+int sell_l_code(int v) { return v < 0 ? 0 : lshape_code(v); }
+int sell_g_code(int v) { return v < 0 ? 0 : kGShapeCode[v]; }
+int sell_l_index(int code) {
+  for (int v = 0; v < kNumLShapes; ++v)
+    if (lshape_code(v) == code) return v;
+  return -1;
+}
+int sell_g_index(int code) {
+  for (int v = 0; v < kNumGShapes; ++v)
+    if (kGShapeCode[v] == code) return v;
+  return -1;
+}
 }  // namespace dec

@@ -369,7 +369,7 @@ def test_batched_variants_are_bit_identical(abi, ctx):
     ref = O.solve_path(wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k, discs=wl.discs,
                        precond="fsai", rtol=1e-13)
     base = None
-    for v in (2, 4, 12, 114, 106, 1004, 2004, 2002):
+    for v in (2, 4, 12, 114, 106, 1004, 2004, 2002, 2512):
         ctx.dec_set_batch_variant(v)
         res = run.run_path(ctx, wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k, discs=wl.discs,
                            mode="batched", rtol=1e-10)
@@ -393,3 +393,29 @@ def test_batched_variants_are_bit_identical(abi, ctx):
     ctx.dec_laplacian_build(wg.T0, abi.DEC_PRECOND_FSAI_SHARED)
     st, _, _ = ctx.dec_solve(1e-10, 1000, abi.DEC_MODE_MIXED_BATCHED, raise_on_error=False)
     assert st == abi.DEC_ERR_ARG
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed_phased"])
+def test_sell_shapes_are_bit_identical(abi, ctx, mode):
+    """The single-instance SELL kernels' launch shapes (register round trips
+    of 4, 8 or 12 entries at 4 or 8 blocks per SM for L; staged or chunked
+    FSAI halves) add every row's entries in the same order: forced one by
+    one they give identical temperatures and iterations, and the
+    autotuner's pick is one of them."""
+    from paper_2104_05999_gb300 import run
+    wl = make_workload("lognormal64", N=20)
+    prec = 0 if mode == "fp64" else 1
+    res0 = run.run_path(ctx, wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k, mode=mode, rtol=1e-10)
+    tuned = ctx.dec_get_sell_variant(prec)
+    assert tuned[0] in (408, 808, 412, 804) and tuned[1] in (14, 8)
+    for l_shape in (408, 808, 412, 804):
+        for g_shape in (14, 8):
+            ctx.dec_set_sell_variant(l_shape, g_shape)
+            res = run.run_path(ctx, wl.xyz, wl.tets, wl.tags, wl.T0, k=wl.k, mode=mode,
+                               rtol=1e-10)
+            assert ctx.dec_get_sell_variant(prec) == (l_shape, g_shape)
+            assert np.array_equal(res.T, res0.T), (l_shape, g_shape)
+            assert np.array_equal(res.iters, res0.iters), (l_shape, g_shape)
+    ctx.dec_set_sell_variant(0, 0)
+    with pytest.raises(abi.DecError):
+        ctx.dec_set_sell_variant(407, 14)
