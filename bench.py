@@ -577,6 +577,41 @@ def fields_measure(n_fields=16, N=64):
             "k_eff_max_rel_diff": float(np.max(np.abs(qb - q64) / np.abs(q64)))}
 
 
+def tet_measure(N=64):
+    """The paper's own tet-centred form (Sec. 2.3 Eq. 11-13 with the flux
+    block eliminated, Sec. 3.1 limiter): faces of the 64^3 jittered Delaunay
+    cube, then the two-point operator solved by FP64 Jacobi PCG to 1e-10 with
+    k = 1; q_in should be 1 (a linear field) where nothing is limited."""
+    import torch
+    from dec_inputs import make_workload
+    from paper_2104_05999_gb300 import abi
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    wl = make_workload("lognormal64", N=N)
+    d = torch.device("cuda", dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(d)  # noqa: E731
+    xyz, tets, tags, T0 = t(wl.xyz), t(wl.tets), t(wl.tags), t(wl.T0[0])
+    ctx = abi.Context(device=dev)
+    ctx.dec_mesh_upload(xyz, tets, tags)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nf = len(ctx.dec_tet_get_faces()[0])
+    faces_ms = 1000 * (time.perf_counter() - t0)
+    times = []
+    for rep in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.dec_tet_solve(T0, kappa=1.0, limiter=1e-8, rtol=1e-10)
+        times.append(1000 * (time.perf_counter() - t0))
+    ctx.close()
+    return {"mesh": f"{N}^3 jittered Delaunay cube ({wl.n} nodes, {wl.m} tets, {nf} faces)",
+            "faces_ms": round(faces_ms, 2), "solve_ms": round(min(times[1:]), 2),
+            "iters": int(res["iters"]), "relres": float(res["relres"]),
+            "limited": int(res["limited"]), "q_in": float(res["q_in"]),
+            "q_out": float(res["q_out"]),
+            "note": "faces_ms includes copying the faces to the host; solve_ms is the whole "
+                    "dec_tet_solve call (face weights, rows, PCG, k_eff)"}
+
+
 # ------------------------------------------------------------- CPU oracle
 def oracle_phases(name, N_s):
     """Run the oracle's whole path, phase by phase, on the complete instance
@@ -766,6 +801,7 @@ def main():
                                    "sample": desc, **detail}
             out["crack_growth"] = crack_growth_measure()
             out["conductivity_fields"] = fields_measure()
+            out["tet_centred"] = tet_measure()
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
