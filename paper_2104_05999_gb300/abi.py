@@ -109,6 +109,14 @@ class DecError(RuntimeError):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
 
 
+def _host_or_tensor(a, dtype):
+    """A torch tensor as it is; anything else as a C-contiguous numpy array
+    of ``dtype`` (keep the result alive while its address is in use)."""
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
 def _ptr(a, dtype):
     """Address of a contiguous numpy array / torch tensor of ``dtype``."""
     if a is None:
@@ -218,8 +226,8 @@ class Context:
         keep = None
         optr = None
         if order is not None:
-            keep = np.ascontiguousarray(order, dtype=np.int32)
-            optr = keep.ctypes.data
+            keep = _host_or_tensor(order, np.int32)
+            optr = _ptr(keep, np.int32)
         st = self.lib.dec_crack_evolve(self.h, int(rule), int(max_steps), optr,
                                        float(rtol), int(max_iter), int(mode),
                                        float(k_stop), cracked.ctypes.data,
@@ -234,11 +242,11 @@ class Context:
         """Stochastic cracking of several paths at once; ``orders`` is
         [n_paths, max_steps].  Returns (status, k_eff per path trimmed to
         its steps, steps per path)."""
-        orders = np.ascontiguousarray(orders, dtype=np.int32)
+        orders = _host_or_tensor(orders, np.int32)
         P, S = orders.shape
         keff = np.zeros((P, max(S, 1)))
         steps = np.zeros(P, dtype=np.int32)
-        st = self.lib.dec_crack_paths(self.h, int(P), int(S), orders.ctypes.data,
+        st = self.lib.dec_crack_paths(self.h, int(P), int(S), _ptr(orders, np.int32),
                                       float(rtol), int(max_iter), float(k_stop),
                                       keff.ctypes.data, steps.ctypes.data)
         if raise_on_error:
@@ -255,12 +263,12 @@ class Context:
         it = C.c_int32()
         rr = C.c_double()
         nl = C.c_int64()
-        cf = None if cracked_faces is None else np.ascontiguousarray(cracked_faces, dtype=np.int32)
+        T0 = _host_or_tensor(T0, np.float64)
+        cf = _host_or_tensor(cracked_faces, np.int32)
+        ff = _host_or_tensor(face_flux, np.float64)
         st = self.lib.dec_tet_solve(
-            self.h, _ptr(np.ascontiguousarray(T0, dtype=np.float64), np.float64),
-            float(kappa), float(limiter), None if cf is None else cf.ctypes.data,
-            0 if cf is None else len(cf),
-            None if face_flux is None else _ptr(np.ascontiguousarray(face_flux, dtype=np.float64), np.float64),
+            self.h, _ptr(T0, np.float64), float(kappa), float(limiter), _ptr(cf, np.int32),
+            0 if cf is None else len(cf), _ptr(ff, np.float64),
             float(rtol), int(max_iter), alpha.ctypes.data, q2.ctypes.data, C.byref(it),
             C.byref(rr), C.byref(nl))
         if raise_on_error:
