@@ -379,7 +379,9 @@ dec_status dec_crack_paths(dec_ctx* ctx, int32_t n_paths, int32_t max_steps,
  * of those nodes and any other boundary face carries the prescribed outward
  * flux (Eq. 13; none: zero flux).  Sec. 3.1's limiter raises *2 entries
  * below `limiter` to it.  Cracked faces (Sec. 2.5) get w_f = 0.  FP64 PCG
- * (Jacobi) from alpha = 0 to ||b - S alpha|| <= rtol ||b||.
+ * from alpha = 0 to ||b - S alpha|| <= rtol ||b||, preconditioned by an
+ * FSAI factor (the sparse approximate inverse family of the paper's
+ * solver; pattern: each tet's lower neighbours and itself).
  *   T0            [n_nodes] f64 host or device: node values (read on
  *                 Dirichlet nodes).
  *   kappa         conductivity, > 0.  limiter: <= 0 for none (e.g. 1e-8).

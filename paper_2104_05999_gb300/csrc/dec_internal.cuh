@@ -197,7 +197,8 @@ struct dec_ctx {
   bool tet_solved = false;
   bool tet_flux = false;                   // the last solve had face fluxes
   dec::DevBuf<int32_t> faces, fslot0, fslot1, t2f;
-  dec::DevBuf<double> tet_h, fw, fT0, tval, trhs, tdinv, talpha, tr, tp, tq, tT0, tflux;
+  dec::DevBuf<double> tet_h, fw, fT0, tval, trhs, talpha, tr, tp, tq, tT0, tflux;
+  dec::DevBuf<double> tglo, tgup, tt;      // FSAI factor of the tet operator (slot-major), t
   dec::DevBuf<uint8_t> fcls, fcut;
   dec::DevBuf<int32_t> tcol, tcracked;
   std::vector<int> iters_host;
@@ -228,7 +229,8 @@ struct dec_ctx {
     kpartial.release(); crack_buf.release(); bx.release(); br.release(); bz.release();
     bp.release(); bq.release(); bt.release();
     faces.release(); fslot0.release(); fslot1.release(); t2f.release(); tet_h.release();
-    fw.release(); fT0.release(); tval.release(); trhs.release(); tdinv.release();
+    fw.release(); fT0.release(); tval.release(); trhs.release();
+    tglo.release(); tgup.release(); tt.release();
     talpha.release(); tr.release(); tp.release(); tq.release(); tT0.release(); tflux.release();
     fcls.release(); fcut.release(); tcol.release(); tcracked.release();
   }

@@ -18,7 +18,8 @@
 // Faces are the sorted node triples of the tets, numbered in lexicographic
 // order: key (edge id of the two smallest nodes, largest node) sorted by the
 // library's radix sort.  The SPD system (at most 5 entries per row) is
-// solved by FP64 PCG with Jacobi in one cooperative kernel.
+// solved by FP64 PCG with an FSAI preconditioner (pattern: each tet's lower
+// neighbours) in one cooperative kernel.
 #include "dec_internal.cuh"
 
 #include <algorithm>
@@ -190,15 +191,15 @@ __global__ void mark_cut_kernel(const int32_t* __restrict__ list, int64_t nl, in
 
 // Row T of the two-point operator in 5 slots (slot 0 the diagonal, slot
 // v + 1 the neighbour across the face opposite vertex v, column -1 when
-// absent), stored slot-major (k * m + T), and its right-hand side.  A tet
-// whose faces all carry w = 0 becomes an identity row with rhs 0.
+// absent or when the face carries w = 0, e.g. cracked), stored slot-major
+// (k * m + T), and its right-hand side.  A tet whose faces all carry w = 0
+// becomes an identity row with rhs 0.
 __global__ void tet_rows_kernel(int64_t m, const int32_t* __restrict__ t2f,
                                 const int32_t* __restrict__ slot0,
                                 const int32_t* __restrict__ slot1, const double* __restrict__ w,
                                 const uint8_t* __restrict__ cls, const double* __restrict__ T0f,
                                 const double* __restrict__ flux, int32_t* __restrict__ col,
-                                double* __restrict__ val, double* __restrict__ rhs,
-                                double* __restrict__ dinv) {
+                                double* __restrict__ val, double* __restrict__ rhs) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
        t += (int64_t)gridDim.x * blockDim.x) {
     double d = 0.0, bt = 0.0;
@@ -208,10 +209,11 @@ __global__ void tet_rows_kernel(int64_t m, const int32_t* __restrict__ t2f,
       int32_t nb = -1;
       double off = 0.0;
       if (cls[f] == 0) {
-        const int32_t other = slot0[f] / 4 == (int32_t)t ? slot1[f] / 4 : slot0[f] / 4;
-        nb = other;
-        off = -wf;
-        d += wf;
+        if (wf != 0.0) {
+          nb = slot0[f] / 4 == (int32_t)t ? slot1[f] / 4 : slot0[f] / 4;
+          off = -wf;
+          d += wf;
+        }
       } else if (cls[f] == 1) {
         d += wf;
         bt += wf * T0f[f];
@@ -228,7 +230,108 @@ __global__ void tet_rows_kernel(int64_t m, const int32_t* __restrict__ t2f,
     col[t] = (int32_t)t;
     val[t] = d;
     rhs[t] = bt;
-    dinv[t] = 1.0 / d;
+  }
+}
+
+// FSAI factor of the tet operator A (the sparse-approximate-inverse family
+// of the paper's ParaSails preconditioner, Sec. 2.3): row T of G has the
+// pattern P = {T's lower neighbours, T}, at most 5 entries, and solves
+// A[P,P] g = e_T, G_T = g / sqrt(g_T); M = G^T G.  Cholesky of the <= 5x5
+// block in FP64; a pivot <= 1e-12 max(diag) (a singular block: a group of
+// tets cut off by cracks) is factored again with that shift on the diagonal.
+// glo[k * m + T] holds G[T][col_k(T)] for the slots k whose column is T
+// (k = 0) or a lower neighbour, 0 elsewhere.
+__device__ __forceinline__ double tet_entry(const int32_t* __restrict__ col,
+                                            const double* __restrict__ val, int64_t m,
+                                            int32_t p, int32_t q) {
+  if (p == q) return val[p];
+#pragma unroll
+  for (int k = 1; k < 5; ++k)
+    if (col[(int64_t)k * m + p] == q) return val[(int64_t)k * m + p];
+  return 0.0;
+}
+
+__global__ void tet_fsai_kernel(int64_t m, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, double* __restrict__ glo) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int32_t P[5];
+    int slot_of[5];
+    int k = 0;
+    for (int s = 1; s < 5; ++s) {
+      const int32_t c = col[(int64_t)s * m + t];
+      if (c >= 0 && c < (int32_t)t) { P[k] = c; slot_of[k] = s; ++k; }
+    }
+    // ascending column order, then T itself last
+    for (int i = 1; i < k; ++i)
+      for (int j = i; j > 0 && P[j - 1] > P[j]; --j) {
+        const int32_t c = P[j]; P[j] = P[j - 1]; P[j - 1] = c;
+        const int sl = slot_of[j]; slot_of[j] = slot_of[j - 1]; slot_of[j - 1] = sl;
+      }
+    P[k] = (int32_t)t;
+    slot_of[k] = 0;
+    const int n = k + 1;
+    double A[5][5];
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j <= i; ++j) A[i][j] = tet_entry(col, val, m, P[i], P[j]);
+      dmax = fmax(dmax, A[i][i]);
+    }
+    const double tiny = 1e-12 * dmax;
+    double Lc[5][5];
+    double shift = 0.0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      bool ok = true;
+      for (int i = 0; i < n && ok; ++i) {
+        for (int j = 0; j <= i; ++j) {
+          double sum = A[i][j] + (i == j ? shift : 0.0);
+          for (int l = 0; l < j; ++l) sum -= Lc[i][l] * Lc[j][l];
+          if (i == j) {
+            if (!(sum > tiny)) { ok = false; break; }
+            Lc[i][i] = sqrt(sum);
+          } else {
+            Lc[i][j] = sum / Lc[j][j];
+          }
+        }
+      }
+      if (ok) break;
+      shift = tiny;
+      if (attempt == 1) {            // give up: the Jacobi row of the block
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j <= i; ++j) Lc[i][j] = i == j ? sqrt(fmax(A[i][i], tiny) + tiny) : 0.0;
+      }
+    }
+    // L y = e_last: y = (0, .., 0, 1 / L_nn); L^T g = y; G = g L_nn
+    double g[5];
+    g[n - 1] = 1.0 / (Lc[n - 1][n - 1] * Lc[n - 1][n - 1]);
+    for (int i = n - 2; i >= 0; --i) {
+      double sum = 0.0;
+      for (int l = i + 1; l < n; ++l) sum += Lc[l][i] * g[l];
+      g[i] = -sum / Lc[i][i];
+    }
+    const double scale = Lc[n - 1][n - 1];
+    for (int s = 0; s < 5; ++s) glo[(int64_t)s * m + t] = 0.0;
+    for (int i = 0; i < n; ++i) glo[(int64_t)slot_of[i] * m + t] = g[i] * scale;
+  }
+}
+
+// G^T in the same slots: gup[0] = G[T][T], gup[k] = G[c][T] for an upper
+// neighbour c of T (found in row c's slot whose column is T).
+__global__ void tet_fsai_upper_kernel(int64_t m, const int32_t* __restrict__ col,
+                                      const double* __restrict__ glo,
+                                      double* __restrict__ gup) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    gup[t] = glo[t];
+    for (int s = 1; s < 5; ++s) {
+      const int32_t c = col[(int64_t)s * m + t];
+      double v = 0.0;
+      if (c > (int32_t)t) {
+        for (int k = 1; k < 5; ++k)
+          if (col[(int64_t)k * m + c] == (int32_t)t) v = glo[(int64_t)k * m + c];
+      }
+      gup[(int64_t)s * m + t] = v;
+    }
   }
 }
 
@@ -238,7 +341,9 @@ struct TetPcgArgs {
   const int32_t* col;
   const double* val;
   const double* rhs;
-  const double* dinv;
+  const double* glo;        // FSAI factor G (slot-major)
+  const double* gup;        // G^T in the same slots
+  double* tt;               // t = G r
   double *x, *r, *p, *q;
   double* partial;          // [2][2][grid]
   unsigned* bar;            // [0] arrivals, [1] generation
@@ -318,9 +423,22 @@ __device__ __forceinline__ double ell_row(const TetPcgArgs& a, int64_t t, const 
   return y;
 }
 
-// PCG (Jacobi) from x = 0 until ||b - A x|| <= rtol ||b||, checked on the
-// true residual; a recursive residual that has converged but a true one that
-// has not restarts from the true residual.
+// sum over the row's slots of G[k][T] x[col_k(T)] (slot 0: x[T])
+__device__ __forceinline__ double fsai_row(const TetPcgArgs& a, const double* G, int64_t t,
+                                           const double* x) {
+  double y = G[t] * x[t];
+#pragma unroll
+  for (int k = 1; k < 5; ++k) {
+    const int32_t c = a.col[k * a.m + t];
+    if (c >= 0) y = fma(G[k * a.m + t], x[c], y);
+  }
+  return y;
+}
+
+// PCG (FSAI M = G^T G) from x = 0 until ||b - A x|| <= rtol ||b||,
+// checked on the true residual; a recursive residual that has converged but
+// a true one that has not restarts from the true residual.  With FSAI the
+// preconditioned residual z lives in q between the update and p = z + beta p.
 __global__ void __launch_bounds__(kTBlock) tet_pcg_kernel(TetPcgArgs a) {
   if (*(volatile unsigned*)(a.bar + 3) && blockIdx.x == gridDim.x - 1) return;
   const int64_t m = a.m;
@@ -328,7 +446,7 @@ __global__ void __launch_bounds__(kTBlock) tet_pcg_kernel(TetPcgArgs a) {
   const int64_t ts = (int64_t)gridDim.x * kTBlock;
   int* err = a.status;
   int parity = 0;
-  double v2[2], t2[2], v1[1], t1[1];
+  double v1[1], t1[1];
   // x = 0, r = b, |b|^2
   double bb = 0.0;
   for (int64_t t = t0; t < m; t += ts) {
@@ -345,10 +463,12 @@ __global__ void __launch_bounds__(kTBlock) tet_pcg_kernel(TetPcgArgs a) {
   double rr_true = bnorm2;
   if (bnorm2 > 0.0) {
     for (;;) {
-      // (re)start: p = z = D^-1 r, rz
+      // (re)start: p = z = M r, rz
       double rz = 0.0;
+      for (int64_t t = t0; t < m; t += ts) a.tt[t] = fsai_row(a, a.glo, t, a.r);
+      if (!tgrid_sync(a.bar, err)) return;
       for (int64_t t = t0; t < m; t += ts) {
-        const double z = a.dinv[t] * a.r[t];
+        const double z = fsai_row(a, a.gup, t, a.tt);
         a.p[t] = z;
         rz = fma(a.r[t], z, rz);
       }
@@ -368,22 +488,31 @@ __global__ void __launch_bounds__(kTBlock) tet_pcg_kernel(TetPcgArgs a) {
         pq = t1[0];
         if (!(pq > 0.0) || !isfinite(pq)) { outcome = 3; break; }   // breakdown
         const double alpha = rz / pq;
-        double rzn = 0.0, rr = 0.0;
+        double rr = 0.0;
         for (int64_t t = t0; t < m; t += ts) {
           a.x[t] = fma(alpha, a.p[t], a.x[t]);
           const double rt = fma(-alpha, a.q[t], a.r[t]);
           a.r[t] = rt;
-          rzn = fma(rt, a.dinv[t] * rt, rzn);
           rr = fma(rt, rt, rr);
         }
-        v2[0] = rzn;
-        v2[1] = rr;
-        if (!tgrid_sum<2>(v2, t2, a.partial, parity, a.bar, err)) return;
+        v1[0] = rr;
+        if (!tgrid_sum<1>(v1, t1, a.partial, parity, a.bar, err)) return;
         ++it;
-        if (t2[1] <= tol2) { conv = true; break; }
-        const double beta = t2[0] / rz;
-        rz = t2[0];
-        for (int64_t t = t0; t < m; t += ts) a.p[t] = fma(beta, a.p[t], a.dinv[t] * a.r[t]);
+        if (t1[0] <= tol2) { conv = true; break; }
+        // z = G^T (G r) into q, r.z
+        for (int64_t t = t0; t < m; t += ts) a.tt[t] = fsai_row(a, a.glo, t, a.r);
+        if (!tgrid_sync(a.bar, err)) return;
+        double rzf = 0.0;
+        for (int64_t t = t0; t < m; t += ts) {
+          const double z = fsai_row(a, a.gup, t, a.tt);
+          a.q[t] = z;
+          rzf = fma(a.r[t], z, rzf);
+        }
+        v1[0] = rzf;
+        if (!tgrid_sum<1>(v1, t1, a.partial, parity, a.bar, err)) return;
+        const double beta = t1[0] / rz;
+        rz = t1[0];
+        for (int64_t t = t0; t < m; t += ts) a.p[t] = fma(beta, a.p[t], a.q[t]);
         if (!tgrid_sync(a.bar, err)) return;
       }
       // true residual r = b - A x
@@ -558,7 +687,9 @@ dec_status tet_solve(dec_ctx* ctx, const double* T0_dev, double kappa, double li
   DEC_TRY(ctx->tcol.ensure(5 * m));
   DEC_TRY(ctx->tval.ensure(5 * m));
   DEC_TRY(ctx->trhs.ensure(m));
-  DEC_TRY(ctx->tdinv.ensure(m));
+  DEC_TRY(ctx->tglo.ensure(5 * m));
+  DEC_TRY(ctx->tgup.ensure(5 * m));
+  DEC_TRY(ctx->tt.ensure(m));
   DEC_TRY(ctx->talpha.ensure(m));
   DEC_TRY(ctx->tr.ensure(m));
   DEC_TRY(ctx->tp.ensure(m));
@@ -578,10 +709,11 @@ dec_status tet_solve(dec_ctx* ctx, const double* T0_dev, double kappa, double li
       T0_dev, ctx->fcut.p, kappa, limiter, ctx->fw.p, ctx->fcls.p, ctx->fT0.p, lim);
   tet_rows_kernel<<<tgrid(ctx, m), 256, 0, s>>>(m, ctx->t2f.p, ctx->fslot0.p, ctx->fslot1.p,
                                                 ctx->fw.p, ctx->fcls.p, ctx->fT0.p, flux_dev,
-                                                ctx->tcol.p, ctx->tval.p, ctx->trhs.p,
-                                                ctx->tdinv.p);
+                                                ctx->tcol.p, ctx->tval.p, ctx->trhs.p);
+  tet_fsai_kernel<<<tgrid(ctx, m), 256, 0, s>>>(m, ctx->tcol.p, ctx->tval.p, ctx->tglo.p);
+  tet_fsai_upper_kernel<<<tgrid(ctx, m), 256, 0, s>>>(m, ctx->tcol.p, ctx->tglo.p, ctx->tgup.p);
   DEC_TRY(cudaGetLastError());
-  ctx->launches += 3;
+  ctx->launches += 5;
   int hflag[4];
   DEC_TRY(cudaMemcpyAsync(hflag, ctx->errflag.p, sizeof(hflag), cudaMemcpyDeviceToHost, s));
   DEC_TRY(cudaStreamSynchronize(s));
@@ -608,7 +740,9 @@ dec_status tet_solve(dec_ctx* ctx, const double* T0_dev, double kappa, double li
   a.col = ctx->tcol.p;
   a.val = ctx->tval.p;
   a.rhs = ctx->trhs.p;
-  a.dinv = ctx->tdinv.p;
+  a.glo = ctx->tglo.p;
+  a.gup = ctx->tgup.p;
+  a.tt = ctx->tt.p;
   a.x = ctx->talpha.p;
   a.r = ctx->tr.p;
   a.p = ctx->tp.p;
