@@ -2,8 +2,9 @@
 Eq. 11-13 with the flux block eliminated; Sec. 3.1 limiter; Eq. 13 Neumann
 flux; Whitney flux vectors) against the oracle's tet_centred_solve and
 whitney_flux.  Bars: faces and the tet->face map bit-exact; potentials within
-1e-8 relative L2 (the oracle solves directly, the GPU by FP64 PCG to 1e-12);
-k_eff within 1e-8."""
+1e-8 relative L2 (the oracle solves directly, the GPU by FP64 PCG with FSAI
+to 1e-11: the true residual of these small cracked systems levels off near
+1e-12 in FP64); k_eff within 1e-8."""
 import numpy as np
 import pytest
 
@@ -49,7 +50,7 @@ def test_linear_field_is_exact_without_the_limiter(ctx):
     # every circumcentre and k_eff = 1
     wl = make_workload("lognormal64", N=7)
     ctx.dec_mesh_upload(wl.xyz, wl.tets, wl.tags)
-    res = ctx.dec_tet_solve(wl.T0[0], limiter=1e-8, rtol=1e-13)
+    res = ctx.dec_tet_solve(wl.T0[0], limiter=1e-8, rtol=1e-11)
     ref = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0], limiter=1e-8)
     assert res["limited"] == ref["limited"] == 0
     np.testing.assert_allclose(res["alpha"], 1.0 - ref["cT"][:, 0], atol=1e-10)
@@ -85,7 +86,7 @@ def test_cracked_faces_and_cut_off_tets(ctx):
     T = int(np.flatnonzero(base["interior"][t2f].all(axis=1))[0])
     cracked = np.unique(np.r_[np.random.default_rng(3).choice(inner, 300, replace=False), t2f[T]])
     ref = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0], cracked_faces=cracked)
-    res = ctx.dec_tet_solve(wl.T0[0], cracked_faces=cracked, rtol=1e-13)
+    res = ctx.dec_tet_solve(wl.T0[0], cracked_faces=cracked, rtol=1e-11)
     assert res["alpha"][T] == 0.0 and ref["alpha"][T] == 0.0
     assert _rel(res["alpha"], ref["alpha"]) <= 1e-8
     assert res["q_in"] == pytest.approx(ref["q_in"], rel=1e-8)
@@ -104,7 +105,7 @@ def test_neumann_flux_and_whitney_vectors(ctx):
     P = wl.xyz[base["faces"]]
     flux = np.where((P[:, :, 0] == 1.0).all(axis=1), base["area"], 0.0)
     ref = O.tet_centred_solve(wl.xyz, wl.tets, tags, wl.T0[0], face_flux=flux)
-    res = ctx.dec_tet_solve(wl.T0[0], face_flux=flux, rtol=1e-13)
+    res = ctx.dec_tet_solve(wl.T0[0], face_flux=flux, rtol=1e-11)
     assert _rel(res["alpha"], ref["alpha"]) <= 1e-8
     np.testing.assert_allclose(res["alpha"], 1.0 - ref["cT"][:, 0], atol=1e-9)
     v = ctx.dec_tet_whitney()
@@ -120,7 +121,7 @@ def test_whitney_with_cracks_matches_oracle(ctx):
                                               replace=False)
     ref = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0], cracked_faces=cracked,
                               kappa=2.5)
-    res = ctx.dec_tet_solve(wl.T0[0], kappa=2.5, cracked_faces=cracked, rtol=1e-13)
+    res = ctx.dec_tet_solve(wl.T0[0], kappa=2.5, cracked_faces=cracked, rtol=1e-11)
     assert _rel(res["alpha"], ref["alpha"]) <= 1e-8
     vref = O.whitney_flux(wl.xyz, wl.tets, ref)
     v = ctx.dec_tet_whitney()
@@ -149,9 +150,32 @@ def test_device_inputs_match_host_inputs(ctx):
     ctx.dec_mesh_upload(wl.xyz, wl.tets, wl.tags)
     faces, _ = ctx.dec_tet_get_faces()
     cracked = np.arange(0, len(faces), 7, dtype=np.int32)
-    host = ctx.dec_tet_solve(wl.T0[0], cracked_faces=cracked, rtol=1e-12)
+    host = ctx.dec_tet_solve(wl.T0[0], cracked_faces=cracked, rtol=1e-11)
     dev = torch.device("cuda", 0)
     res = ctx.dec_tet_solve(torch.from_numpy(wl.T0[0].copy()).to(dev),
-                            cracked_faces=torch.from_numpy(cracked).to(dev), rtol=1e-12)
+                            cracked_faces=torch.from_numpy(cracked).to(dev), rtol=1e-11)
     assert np.array_equal(res["alpha"], host["alpha"])
     assert res["q_in"] == host["q_in"]
+
+
+def test_cut_off_pair_keeps_zero_potential(ctx):
+    # two neighbouring tets cut off from the rest by cracks on their other
+    # six faces: a singular 2x2 block with zero right-hand side (the FSAI
+    # factor meets a zero pivot there and takes the shifted factorisation);
+    # both potentials stay 0, as the oracle's anchored solve gives, and the
+    # rest matches the oracle
+    wl = make_workload("lognormal64", N=8)
+    ctx.dec_mesh_upload(wl.xyz, wl.tets, wl.tags)
+    base = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0])
+    t2f, owner = base["t2f"], base["owner"]
+    inner = base["interior"]
+    T1 = next(t for t in range(len(wl.tets)) if inner[t2f[t]].all()
+              and all(inner[t2f[o]].all() for o in owner[t2f[t]].ravel() if o != t))
+    f = t2f[T1][0]
+    T2 = int(owner[f][0] if owner[f][1] == T1 else owner[f][1])
+    cracked = np.setdiff1d(np.r_[t2f[T1], t2f[T2]], [f]).astype(np.int32)
+    ref = O.tet_centred_solve(wl.xyz, wl.tets, wl.tags, wl.T0[0], cracked_faces=cracked)
+    res = ctx.dec_tet_solve(wl.T0[0], cracked_faces=cracked, rtol=1e-11)
+    assert ref["alpha"][T1] == 0.0 and ref["alpha"][T2] == 0.0
+    assert res["alpha"][T1] == 0.0 and res["alpha"][T2] == 0.0
+    assert _rel(res["alpha"], ref["alpha"]) <= 1e-8
