@@ -425,13 +425,16 @@ cudaError_t init_kernel_attributes() {
   return e;
 }
 
-// k_eff pieces of every instance in one pass: block row blockIdx.y is
-// instance b (its crack state when `states`, its Dirichlet set when `sets`),
-// T = u_b + T0 on Dirichlet nodes formed on the fly; block partials go to
-// partial[(3 b + v) * gridDim.x + block] and k_eff_batch_sum_kernel adds them
-// in block order (deterministic).
+// k_eff pieces of every instance: block row blockIdx.y takes instances
+// kKeffGroup * y ... (crack state b when `states`, Dirichlet set b when
+// `sets`, field b when `fields`), reading each row's structure and edge data
+// once for the whole group; T = u_b + T0 on Dirichlet nodes is formed on the
+// fly.  Block partials go to partial[(3 b + v) * gridDim.x + block] and
+// k_eff_batch_sum_kernel adds them in block order (deterministic).
+constexpr int kKeffGroup = 8;
+
 __global__ void __launch_bounds__(kBlock)
-k_eff_batch_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+k_eff_batch_kernel(int64_t n, int B, const int32_t* __restrict__ rowptr,
                    const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
                    const int32_t* __restrict__ dpos, const uint8_t* __restrict__ tag,
                    const double* __restrict__ xyz, const double* __restrict__ w0,
@@ -439,37 +442,59 @@ k_eff_batch_kernel(int64_t n, const int32_t* __restrict__ rowptr,
                    int fields, const double* __restrict__ u, const double* __restrict__ T0,
                    double* __restrict__ partial) {
   __shared__ double sh[kBlock];
-  const int b = blockIdx.y;
-  const int state = states ? b : 0;
-  const double* w = w0 + (fields ? (int64_t)b * ne : 0);   // this instance's *1
-  const double* ub = u + (int64_t)b * n;
-  const double* t0 = T0 + (sets ? (int64_t)b * n : 0);
-  auto Tof = [&](int64_t i) { return ub[i] + (tag[i] == DEC_NODE_DIRICHLET ? t0[i] : 0.0); };
-  double qin = 0.0, qout = 0.0, en = 0.0;
+  const int g0 = blockIdx.y * kKeffGroup;
+  const int gn = min(kKeffGroup, B - g0);
+  auto Tof = [&](int b, int64_t i) {
+    const double* t0 = T0 + (sets ? (int64_t)b * n : 0);
+    return u[(int64_t)b * n + i] + (tag[i] == DEC_NODE_DIRICHLET ? t0[i] : 0.0);
+  };
+  double qin[kKeffGroup], qout[kKeffGroup], en[kKeffGroup];
+#pragma unroll
+  for (int j = 0; j < kKeffGroup; ++j) qin[j] = qout[j] = en[j] = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double Ti = Tof(i);
+    double Ti[kKeffGroup], net[kKeffGroup];
+#pragma unroll
+    for (int j = 0; j < kKeffGroup; ++j) {
+      Ti[j] = j < gn ? Tof(g0 + j, i) : 0.0;
+      net[j] = 0.0;
+    }
     const int32_t k0 = rowptr[i], k1 = rowptr[i + 1], kd = dpos[i];
-    double net = 0.0;
     for (int32_t k = k0; k < k1; ++k) {
       if (k == kd) continue;
       const int32_t e = eid[k];
-      const double we = (int)fc[e] > state ? w[e] : 0.0;
-      const double d = Ti - Tof(col[k]);
-      net += we * d;
-      if (k > kd) en += we * d * d;
+      const int32_t c = col[k];
+      const int f = (int)fc[e];
+      const double ws = fields ? 0.0 : w0[e];
+#pragma unroll
+      for (int j = 0; j < kKeffGroup; ++j) {
+        if (j >= gn) break;
+        const int b = g0 + j;
+        const double wb = fields ? w0[(int64_t)b * ne + e] : ws;
+        const double we = f > (states ? b : 0) ? wb : 0.0;
+        const double d = Ti[j] - Tof(b, c);
+        net[j] += we * d;
+        if (k > kd) en[j] += we * d * d;
+      }
     }
     if (tag[i] == DEC_NODE_DIRICHLET) {
       const double xi = xyz[3 * i];
-      if (xi == 0.0) qin += net;
-      else if (xi == 1.0) qout -= net;
+#pragma unroll
+      for (int j = 0; j < kKeffGroup; ++j) {
+        if (xi == 0.0) qin[j] += net[j];
+        else if (xi == 1.0) qout[j] -= net[j];
+      }
     }
   }
-  const double v[3] = {qin, qout, en};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double t = block_sum<kBlock>(v[k], sh);
-    if (threadIdx.x == 0) partial[(3 * (int64_t)b + k) * gridDim.x + blockIdx.x] = t;
+  for (int j = 0; j < kKeffGroup; ++j) {
+    const double v[3] = {qin[j], qout[j], en[j]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double t = block_sum<kBlock>(v[k], sh);
+      if (threadIdx.x == 0 && j < gn)
+        partial[(3 * (int64_t)(g0 + j) + k) * gridDim.x + blockIdx.x] = t;
+    }
   }
 }
 
@@ -492,12 +517,12 @@ dec_status k_eff_all(dec_ctx* ctx, double* out3_host) {
   const int B = ctx->B;
   cudaStream_t s = ctx->stream;
   const unsigned G = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((n + kBlock - 1) / kBlock,
-                           (int64_t)ctx->num_sms * (B >= 8 ? 1 : 4)));
+      1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)ctx->num_sms * 4));
+  const unsigned GY = (unsigned)((B + kKeffGroup - 1) / kKeffGroup);
   DEC_TRY(ctx->kpartial.ensure((size_t)3 * B * G));
   DEC_TRY(ctx->out3.ensure(3 * (size_t)B + 2));
-  k_eff_batch_kernel<<<dim3(G, (unsigned)B), kBlock, 0, s>>>(
-      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->xyz.p, ctx->w.p,
+  k_eff_batch_kernel<<<dim3(G, GY), kBlock, 0, s>>>(
+      n, B, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->tag.p, ctx->xyz.p, ctx->w.p,
       ctx->ne, ctx->first_cut.p, ctx->n_scales > 1, ctx->n_sets > 1, ctx->n_fields > 1,
       ctx->u.p, ctx->T0.p, ctx->kpartial.p);
   k_eff_batch_sum_kernel<<<(unsigned)((3 * B + 3) / 4), 128, 0, s>>>(
