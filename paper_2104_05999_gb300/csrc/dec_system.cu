@@ -207,14 +207,14 @@ constexpr int kPacked = kFsaiThread * (kFsaiThread + 1) / 2;
 
 __device__ __forceinline__ int tri(int a, int b) { return a * (a + 1) / 2 + b; }
 
+template <typename T>
 __device__ void fsai_gather_thread(int k, const int32_t* P, int stride,
                                    const int32_t* __restrict__ rowptr,
                                    const int32_t* __restrict__ dpos,
                                    const int32_t* __restrict__ col,
-                                   const double* __restrict__ val, double* A,
-                                   double shift) {
+                                   const double* __restrict__ val, T* A, T shift) {
   for (int a = 0; a < k; ++a) {
-    for (int b = 0; b <= a; ++b) A[tri(a, b) * stride] = 0.0;
+    for (int b = 0; b <= a; ++b) A[tri(a, b) * stride] = T(0);
     const int32_t r = P[a * stride];
     // lower part of row r (columns <= r, sorted) merged with P[0..a]
     int b = 0;
@@ -222,28 +222,34 @@ __device__ void fsai_gather_thread(int k, const int32_t* P, int stride,
     for (int32_t kk = rowptr[r]; kk <= kend; ++kk) {
       const int32_t c = col[kk];
       while (b < a && P[b * stride] < c) ++b;
-      if (P[b * stride] == c) A[tri(a, b) * stride] = val[kk];
+      if (P[b * stride] == c) A[tri(a, b) * stride] = (T)val[kk];
     }
     A[tri(a, a) * stride] += shift;
   }
 }
 
-__device__ bool fsai_chol_thread(int k, double* A, int stride, double pivot_min) {
+template <typename T>
+__device__ bool fsai_chol_thread(int k, T* A, int stride, T pivot_min) {
   for (int c = 0; c < k; ++c) {
-    const double d = A[tri(c, c) * stride];
+    const T d = A[tri(c, c) * stride];
     if (!(d > pivot_min)) return false;
-    const double lc = sqrt(d);
-    const double inv = 1.0 / lc;
+    const T lc = sqrt(d);
+    const T inv = T(1) / lc;
     A[tri(c, c) * stride] = lc;
     for (int r = c + 1; r < k; ++r) A[tri(r, c) * stride] *= inv;
     for (int r = c + 1; r < k; ++r) {
-      const double lrc = A[tri(r, c) * stride];
+      const T lrc = A[tri(r, c) * stride];
       for (int q = c + 1; q <= r; ++q) A[tri(r, q) * stride] -= lrc * A[tri(q, c) * stride];
     }
   }
   return true;
 }
 
+// T = double: the factor of the FP64 solves.  T = float: the factor the
+// batched solve keeps only in BF16 (its rounding dominates the FP32 one),
+// with the pivot guard of the per-instance FP32 factors (pivot <= 1e-6
+// max(diag): factored again with a 1e-5 max(diag) shift).
+template <typename T>
 __global__ void __launch_bounds__(kFsaiTpb)
 fsai_setup_thread_kernel(int64_t n, const int32_t* __restrict__ rowptr,
                          const int32_t* __restrict__ col, const int32_t* __restrict__ eid,
@@ -252,8 +258,10 @@ fsai_setup_thread_kernel(int64_t n, const int32_t* __restrict__ rowptr,
                          const double* __restrict__ val, double* __restrict__ g64,
                          int32_t* __restrict__ big_rows, int32_t* __restrict__ big_count) {
   extern __shared__ double smem[];
-  double* A = smem + threadIdx.x;                          // stride kFsaiTpb
-  int32_t* P = (int32_t*)(smem + kPacked * kFsaiTpb) + threadIdx.x;
+  T* A = reinterpret_cast<T*>(smem) + threadIdx.x;         // stride kFsaiTpb
+  int32_t* P = (int32_t*)(reinterpret_cast<T*>(smem) + kPacked * kFsaiTpb) + threadIdx.x;
+  constexpr bool f64 = sizeof(T) == sizeof(double);
+  const T pivot_rel = f64 ? T(kPivotRel) : T(1e-6), shift_rel = f64 ? T(kShiftRel) : T(1e-5);
   const int stride = kFsaiTpb;
   for (int64_t i = blockIdx.x * (int64_t)kFsaiTpb + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kFsaiTpb) {
@@ -264,21 +272,21 @@ fsai_setup_thread_kernel(int64_t n, const int32_t* __restrict__ rowptr,
       continue;
     }
     for (int a = 0; a < k; ++a) P[a * stride] = col[k0 + a];
-    fsai_gather_thread(k, P, stride, rowptr, dpos, col, val, A, 0.0);
-    double dmax = 0.0;
+    fsai_gather_thread<T>(k, P, stride, rowptr, dpos, col, val, A, T(0));
+    T dmax = T(0);
     for (int a = 0; a < k; ++a) dmax = fmax(dmax, A[tri(a, a) * stride]);
-    if (!fsai_chol_thread(k, A, stride, kPivotRel * dmax)) {
-      fsai_gather_thread(k, P, stride, rowptr, dpos, col, val, A, kShiftRel * dmax);
-      fsai_chol_thread(k, A, stride, 0.0);
+    if (!fsai_chol_thread<T>(k, A, stride, pivot_rel * dmax)) {
+      fsai_gather_thread<T>(k, P, stride, rowptr, dpos, col, val, A, shift_rel * dmax);
+      fsai_chol_thread<T>(k, A, stride, T(0));
     }
     // C^T g = e_k, g_j stored over the used diagonal slot C_jj
     for (int j = k - 1; j >= 0; --j) {
-      double sum = (j == k - 1) ? 1.0 : 0.0;
+      T sum = (j == k - 1) ? T(1) : T(0);
       for (int r = j + 1; r < k; ++r) sum -= A[tri(r, j) * stride] * A[tri(r, r) * stride];
       A[tri(j, j) * stride] = sum / A[tri(j, j) * stride];
     }
     for (int a = 0; a < k; ++a) {
-      const double g = A[tri(a, a) * stride];
+      const double g = (double)A[tri(a, a) * stride];
       g64[k0 + a] = g;
       if (a < k - 1) g64[pos_up[eid[k0 + a]]] = g;
     }
@@ -343,16 +351,24 @@ dec_status build_precond(dec_ctx* ctx, int vs) {
   int32_t* big_count = ctx->big_rows.p + n;
   DEC_TRY(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
   DEC_TRY(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s));
-  const size_t smem = (size_t)kPacked * kFsaiTpb * sizeof(double) +
+  // the batched solve keeps only a BF16 copy of its shared factor: FP32 set-up
+  const bool f32 = ctx->precond == DEC_PRECOND_FSAI_SHARED;
+  const size_t smem = (size_t)kPacked * kFsaiTpb * (f32 ? sizeof(float) : sizeof(double)) +
                       (size_t)kFsaiThread * kFsaiTpb * sizeof(int32_t);
-  DEC_TRY(cudaFuncSetAttribute(fsai_setup_thread_kernel,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const void* fk = f32 ? (const void*)fsai_setup_thread_kernel<float>
+                       : (const void*)fsai_setup_thread_kernel<double>;
+  DEC_TRY(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned gt = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((n + kFsaiTpb - 1) / kFsaiTpb,
                            (int64_t)ctx->num_sms * std::max<int64_t>(1, (220 << 10) / smem)));
-  fsai_setup_thread_kernel<<<gt, kFsaiTpb, smem, s>>>(
-      n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->pos_up.p, val, g,
-      ctx->big_rows.p, big_count);
+  if (f32)
+    fsai_setup_thread_kernel<float><<<gt, kFsaiTpb, smem, s>>>(
+        n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->pos_up.p, val, g,
+        ctx->big_rows.p, big_count);
+  else
+    fsai_setup_thread_kernel<double><<<gt, kFsaiTpb, smem, s>>>(
+        n, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p, ctx->pos_up.p, val, g,
+        ctx->big_rows.p, big_count);
   fsai_setup_list_kernel<<<(unsigned)ctx->num_sms * 4, 32 * kFsaiWarps, 0, s>>>(
       ctx->big_rows.p, big_count, ctx->rowptr.p, ctx->col.p, ctx->eid.p, ctx->dpos.p,
       ctx->pos_up.p, val, g, ctx->errflag.p);
