@@ -772,11 +772,18 @@ def main():
     ap.add_argument("--mode", default="auto",
                     choices=["auto", "fp64", "mixed", "mixed_phased", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tet-only", action="store_true",
+                    help="only the tet-centred form's measurement (lattice --N, default 64)")
     # lattice size of the complete small instance the oracle runs: per
     # reference-arm step, and for the GPU arm's cpu_baseline
     ap.add_argument("--ref-N", type=int, default=14)
     ap.add_argument("--baseline-N", type=int, default=24)
     args = ap.parse_args()
+    if args.tet_only:
+        from paper_2104_05999_gb300 import _build
+        _build.build()
+        print(json.dumps(tet_measure(N=args.N or 64)), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
